@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark: beam-splitter MPO updates/s of the U(1) MPO mesh on GB300.
+
+One step = one pass of the whole hot path over one batch of synthetic input: the
+state is restored to the lossy squeezed initial MPO (device copy) and the whole
+Clements mesh is applied (every gate: bookkeeping, Fock tables, Theta contraction,
+Gram, eigensolver, keep-chi selection, re-split with entropy), then the final phase
+screen.  The mesh is a plan (gate list resident in HBM, captured in a CUDA graph).
+`value` = gates applied per second of device time (CUDA events on the library's
+stream), L2 flushed by a 512 MiB write before every timed step (not timed).
+`e2e` = the same metric through mpo_sweep_mesh with host buffers (pinned staging,
+gate list H2D and per-gate discarded weights D2H inside the timed region).
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on a
+bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): replicas only -- every rank runs its own instance(s), no
+collective on the data path; value = all ranks' gates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "beam-splitter MPO updates/s at (M,d,chi); mixed vs FP64 at stated observable error"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor = tensor) nominal: 152 SMs x 2.07 GHz x ~4 flop/clk
+ORACLE_SAMPLE_GATES = {"exact_M4_d4": 6, "M16_d6_chi64": 120, "M32_d8_chi256": 12,
+                       "batched_64x_M16_d6": 60, "M48_d8_chi512": 6}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        t0, t1 = (self.marks + [0, 0])[:2] if len(self.marks) >= 2 else (0, time.time())
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = [(t, l) for t, l in self.lines if t0 - 0.25 <= t <= t1 + 0.25] or self.lines[-3:]
+        for _, l in rows:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(name: str, n_gates: int, repeats: int = 1) -> dict:
+    env = dict(os.environ)
+    env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-m", "oracle.timing", name, str(n_gates), str(repeats)],
+                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def workload_arrays(wl, rank: int):
+    """(instances, meshes) for this rank; batched workloads shift their seeds by rank."""
+    import gbs_workloads as w
+    if wl.batch > 1 and rank > 0:
+        wl = w.batched_instances(n=wl.batch, first_seed=100 + rank * wl.batch)
+    meshes = [wl.mesh(i) for i in range(wl.batch)]
+    return wl, meshes
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import gbs_workloads as w
+    wl = w.workload(args.workload)
+    n = ORACLE_SAMPLE_GATES.get(args.workload, 12)
+    res = oracle_sample(args.workload, n, repeats=args.warmup + args.steps)
+    t = res["seconds"][args.warmup:] or res["seconds"]
+    ms = 1e3 * float(np.mean(t))
+    val = n / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "M": wl.M, "d": wl.d, "chi": wl.chi, "instances": 1,
+                   "sample_gates": n},
+        "cpu_baseline": {"value": val, "unit": "updates/s", "cores": res["cores"], "kind": "oracle",
+                         "sample": f"first {n} gates of instance 0's mesh from the initial state, per step"},
+        "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, ws, rank, local):
+    import torch
+    import gbs_workloads as w
+    import paper_2301_12814_gb300 as lib
+    from paper_2301_12814_gb300 import build as libbuild
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl0 = w.workload(args.workload)
+    wl, meshes = workload_arrays(wl0, rank)
+    prec = args.precision or wl.precision
+    if prec not in lib.mpo.PRECISIONS:
+        prec = "fp64"
+    n_gates = [m.n_gates for m in meshes]
+    k = np.concatenate([m.k for m in meshes]).astype(np.int32)
+    th = np.concatenate([m.theta for m in meshes])
+    ph = np.concatenate([m.phi for m in meshes])
+    fp = np.concatenate([m.final_phase for m in meshes])
+    units = int(sum(n_gates))
+    stream = torch.cuda.Stream(device=dev)
+    G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=prec, stream=stream)
+    plan = G.plan_mesh(n_gates, k, th, ph, fp)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        G.reset(); plan.run()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    clocks.mark()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        G.reset()
+        plan.run()
+        ev[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks.mark()
+    time.sleep(0.3)
+    clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * units * args.steps / (tot_ms / 1e3)
+    disc = plan.discarded()
+
+    # per-stage breakdown and algorithmic flops: one instrumented replay (not timed above)
+    G.reset()
+    prof = plan.profile()
+    # end to end through the public API with host buffers
+    e2e_t = []
+    for i in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        G.reset()
+        d_host = G.sweep_mesh(n_gates, k, th, ph, fp)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = units / float(np.mean(e2e_t))
+    if ws > 1:
+        t = torch.tensor([float(np.mean(e2e_t))], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = ws * units / float(t.item())
+    assert np.array_equal(d_host, disc), "sweep and plan disagree"
+    tr, n1, n2 = G.observables()
+    S, pur, smax = G.operator_entropy()
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    # roofline on the dominant stage (all stages are FP64 SIMT in this path)
+    stage = max(("theta", "gram", "eig", "resplit"), key=lambda s: prof[s][0])
+    ms_s, nl_s, fl_s = prof[stage]
+    achieved = fl_s / (ms_s / 1e3) / 1e12 if ms_s > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_{stage}", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 nominal (152 SMs x 2.07 GHz), not in MEASURED_PEAKS.json",
+                "traffic": None, "flops_per_launch": fl_s / max(1, nl_s),
+                "avg_launch_ms": ms_s / max(1, nl_s)}
+    # CPU oracle on a bounded sample (host cores, single BLAS thread)
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        n = ORACLE_SAMPLE_GATES.get(args.workload, 12)
+        try:
+            res = oracle_sample(args.workload, n)
+            cpu = {"value": res["updates_per_s"][0], "unit": "updates/s", "cores": res["cores"], "kind": "oracle",
+                   "sample": f"first {n} gates of instance 0's mesh from the initial state ({res['seconds'][0]:.1f} s)"}
+        except Exception as e:  # the baseline is reported, never a reason to lose the GPU line
+            cpu = {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {str(e)[-200:]}"}
+    h2d = 32 * units + 8 * wl.batch * wl.M
+    d2h = 8 * units + 16
+    line = {
+        "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else prec,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "M": wl.M, "d": wl.d, "chi": wl.chi, "instances": wl.batch,
+                   "gates_per_step": units, "precision": prec,
+                   "r": float(wl.r[0, 0]), "eta": float(wl.eta[0, 0]), "seeds": wl.seeds[:4],
+                   "l2": "flushed: 512 MiB write before each timed step (untimed)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": plan.launches * args.steps,
+        "clocks": clocks.summary(),
+        "stages_ms": {s: round(v[0], 4) for s, v in prof.items()},
+        "stages_gflop": {s: round(v[2] / 1e9, 4) for s, v in prof.items() if v[2] > 0},
+        "wall_s": wall,
+        "observables": {"trace": float(tr[0]), "discarded_sum": float(np.sum(disc[:n_gates[0]])),
+                        "S_max": float(smax[0])},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="M16_d6_chi64")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_native(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

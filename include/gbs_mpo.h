@@ -1,0 +1,170 @@
+/*
+ * gbs_mpo.h -- C ABI of the GB300 (sm_103a) U(1)-symmetric MPO beam-splitter mesh.
+ *
+ * The library simulates lossy Gaussian boson sampling as in Liu et al.,
+ * "Simulating lossy Gaussian boson sampling with matrix product operators"
+ * (arXiv:2301.12814): the lossy squeezed input state is held as a vectorised
+ * density operator in U(1)-symmetric Vidal MPO form (App. D), and every
+ * nearest-neighbour beam splitter of a mesh is applied by the two-site update
+ * of App. D (Eq. `theta` contraction per new centre charge, SVD of every charge
+ * block, global keep-chi truncation, re-split Gamma = V / lambda).
+ *
+ * Conventions shared by every call
+ *   modes     j = 0..M-1; bond b = 0..M sits left of mode b (bond 0 = left edge).
+ *   charge    every bond index carries the pair (c, cbar) = (ket, bra) photons to
+ *             the RIGHT of the bond (App. D), 0 <= c, cbar <= n_cap.
+ *   gate k    acts on modes (k, k+1) with the 2x2 mode matrix
+ *             [[e^{i phi} cos theta, -sin theta], [e^{i phi} sin theta, cos theta]],
+ *             i.e. a_k^dag -> S00 a_k^dag + S10 a_{k+1}^dag (Clements' T block).
+ *   memory    every pointer argument is a HOST pointer unless stated otherwise.
+ *             Inputs are copied before the call returns; outputs are written by
+ *             the time the call returns.  The handle owns all device memory.
+ *   streams   all device work of a handle is issued on params.cuda_stream.
+ *             Calls that return host results synchronise that stream; the
+ *             plan/reset calls are asynchronous.
+ *   threads   one host thread at a time per handle.
+ *   errors    return codes only.  After MPO_ERR_NUMERIC, MPO_ERR_CAPACITY,
+ *             MPO_ERR_INTERNAL or MPO_ERR_CUDA the handle is poisoned: every call
+ *             but mpo_destroy returns MPO_ERR_POISONED.
+ */
+#ifndef GBS_MPO_H
+#define GBS_MPO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpo_ctx* mpo_handle;
+typedef struct mpo_plan_s* mpo_plan;
+
+typedef enum {
+  MPO_OK = 0,
+  MPO_ERR_ARG = 1,       /* invalid argument: sizes, ranges, null pointers        */
+  MPO_ERR_OOM = 2,       /* device allocation failed                             */
+  MPO_ERR_CUDA = 3,      /* a CUDA runtime call failed                           */
+  MPO_ERR_NUMERIC = 4,   /* eigensolver sweep cap reached or a non-finite value  */
+  MPO_ERR_TIMEOUT = 5,   /* reserved: a bounded device wait ran out              */
+  MPO_ERR_CAPACITY = 6,  /* a per-gate workspace bound was exceeded on device    */
+  MPO_ERR_INTERNAL = 7,  /* a device-side consistency check failed               */
+  MPO_ERR_POISONED = 8,  /* handle unusable after an earlier device-side error   */
+  MPO_ERR_NOT_BUILT = 9  /* the CUDA library could not be loaded or has no GPU   */
+} mpo_status;
+
+typedef enum {
+  MPO_FP64 = 0,        /* every step in float64 / complex128                              */
+  MPO_MIXED_TF32 = 1,  /* contraction and Gram products in FP32-accurate tensor/FP32
+                          arithmetic, eigen refinement, threshold, lambda and entropy
+                          in FP64                                                         */
+  MPO_MIXED_BF16 = 2   /* as MIXED_TF32 with BF16-split operands                          */
+} mpo_precision;
+
+typedef struct {
+  int M;              /* modes, 2 <= M <= 256                                        */
+  int d;              /* local Fock cutoff: photon numbers 0..d-1 per mode, 2..32    */
+  int n_cap;          /* cap on total ket (and bra) photons; <= 0 means d - 1;
+                         must satisfy n_cap <= d - 1 and n_cap <= 15                 */
+  int batch;          /* independent instances held by the handle, >= 1             */
+  mpo_precision prec; /* arithmetic of the gate pipeline                             */
+  const int* chi_max; /* [batch] host: bond-dimension cap per instance; a value <= 0
+                         means "no cap" (exact, only values below the numerical
+                         floor are dropped); NULL means no cap for every instance   */
+  void* cuda_stream;  /* cudaStream_t for all work of the handle; NULL = default    */
+} mpo_params;
+
+/* Create a handle and build the initial state of every instance (App. B/C: each
+ * mode starts as single-mode squeezed vacuum c_{2j} ~ (-tanh r)^j, truncated at d,
+ * sent through a pure-loss channel of transmission eta; uniform loss commutes with
+ * the mesh and is applied to the input, Method section).  The state is
+ * rho_0 = P_cap (x)_j rho_j P_cap / Tr, written in exactly canonical U(1) Vidal form
+ * with the bond-0 index ranging over the total-charge pairs.
+ *   r   [batch*M] squeezing per instance and mode (r = 0: vacuum), 0 <= r <= 3
+ *   eta [batch*M] transmission per instance and mode, 0 <= eta <= 1
+ * On success *out owns the device state and a snapshot used by mpo_reset.
+ * Synchronises the stream. */
+mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p,
+                                   const double* r, const double* eta);
+
+/* Restore every instance to the state built by mpo_init_lossy_squeezed
+ * (device-to-device copy on the stream; asynchronous). */
+mpo_status mpo_reset(mpo_handle h);
+
+/* Apply one beam splitter (k, theta, phi) to instance inst: the two-site U(1)
+ * update of App. D (Eq. `theta`, block SVD, keep chi, Gamma = V / lambda).
+ *   discarded_weight  nullable host pointer: sum of dropped s^2 / sum of all s^2.
+ * Synchronises the stream when discarded_weight is non-NULL. */
+mpo_status mpo_apply_bs(mpo_handle h, int inst, int k, double theta, double phi,
+                        double* discarded_weight);
+
+/* Apply a whole mesh to every instance.  Instance i's gates are the n_gates[i]
+ * consecutive entries of k/theta/phi after those of instances 0..i-1, in
+ * application order (U = D T_L ... T_1).  Gates on disjoint mode pairs are
+ * grouped into layers and every layer of every instance runs in one batched pass.
+ *   final_phase  [batch*M] or NULL: phase screen D applied after the last gate.
+ *   discarded    [sum n_gates] or NULL: per-gate discarded weight, same order.
+ * Copies the gate list to the device through a pinned staging buffer owned by the
+ * handle, runs, copies the results back the same way; synchronises. */
+mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k,
+                          const double* theta, const double* phi,
+                          const double* final_phase, double* discarded);
+
+/* Plans: the same mesh as mpo_sweep_mesh, uploaded once and captured in a CUDA
+ * graph; mpo_plan_run replays it asynchronously on the handle's stream with the
+ * gate list already resident in device memory.  A plan belongs to its handle. */
+mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k,
+                         const double* theta, const double* phi,
+                         const double* final_phase, mpo_plan* out);
+mpo_status mpo_plan_run(mpo_plan p);
+/* Per-gate discarded weights of the last run ([sum n_gates], host); synchronises. */
+mpo_status mpo_plan_discarded(mpo_plan p, double* discarded);
+/* Number of kernel launches one mpo_plan_run performs. */
+int mpo_plan_launches(mpo_plan p);
+/* Stages of one gate layer, in launch order (plus the final phase screen). */
+#define MPO_NSTAGES 7
+/* Replay the plan once without the graph, with a CUDA event between consecutive
+ * stage launches on the handle's stream, and report per stage (setup, theta, gram,
+ * eig, select, resplit, phases) the summed device time in ms, the launch count and
+ * the real flops of the executed form (theta: complex MACs of Eq. `theta` over the
+ * contracted blocks x 8; gram: upper triangle x 8 x inner size; eig: 54 x n per
+ * applied Jacobi rotation; resplit: 8 x rows x cols per kept vector).  Each array
+ * is [MPO_NSTAGES] host memory and nullable.  Same results as mpo_plan_run.
+ * Synchronises. */
+mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
+                            double* stage_flops);
+void mpo_plan_destroy(mpo_plan p);
+
+/* Observables of every instance (once per mesh; trace environments):
+ *   trace   [batch]    Tr rho (its deficit 1 - Tr rho is the truncation error proxy)
+ *   n_mean  [batch*M]  <n_j>
+ *   n2_mean [batch*M]  <n_j^2>
+ * normalize_by_trace != 0 divides the moments by Tr rho.  Synchronises. */
+mpo_status mpo_observables(mpo_handle h, double* trace, double* n_mean, double* n2_mean,
+                           int normalize_by_trace);
+
+/* Operator entanglement of the U(1) MPO at every bond (Method, Eq. `schmidt`;
+ * App. B: p = lambda^2 / sum lambda^2, S = -sum p log2 p):
+ *   S             [batch*(M+1)]  bonds 0..M
+ *   purity        [batch*(M+1)]  sum lambda^2 per bond, nullable
+ *   S_max_running [batch]        max over bonds of S, nullable
+ * Synchronises. */
+mpo_status mpo_operator_entropy(mpo_handle h, double* S, double* purity,
+                                double* S_max_running);
+
+/* Bond data of one instance (tests and inspection): chi [M+1] dimensions;
+ * lam [(M+1)*ld] and charge [(M+1)*ld*2] (c, cbar per index), row b holding bond
+ * b's chi[b] entries; either may be NULL.  ld >= largest chi.  Synchronises. */
+mpo_status mpo_get_bonds(mpo_handle h, int inst, int ld, int* chi, double* lam, int* charge);
+
+/* Device pointers/sizes for callers that manage their own buffers: the bond
+ * capacity D (Gamma matrices are D x D) and the number of instances. */
+int mpo_bond_capacity(mpo_handle h);
+
+/* Synchronise the handle's stream and report any device-side error. */
+mpo_status mpo_sync(mpo_handle h);
+
+void mpo_destroy(mpo_handle h);
+const char* mpo_status_string(mpo_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBS_MPO_H */

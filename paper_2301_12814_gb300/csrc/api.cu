@@ -1,0 +1,632 @@
+// C ABI of the GB300 U(1) MPO beam-splitter mesh (declared in include/gbs_mpo.h).
+//
+// Host responsibilities only: argument checks, device memory ownership, the layer
+// schedule of a mesh (gates on disjoint mode pairs commute and run in one batched
+// pass, the single-GPU form of the paper's gate-level parallelism, App. D.4),
+// CUDA-graph capture of a planned mesh, and polling of the device error flag.
+// Every arithmetic step of the method runs in the kernels of init.cu, gate.cu and
+// obs.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gbs_mpo.h"
+#include "mpo_internal.cuh"
+
+size_t eig_smem_bytes(int D);
+cudaError_t gate_module_init();
+
+struct mpo_ctx {
+  int M = 0, d = 0, ncap = 0, B = 0, P = 0, Pc = 0, D = 0;
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* state = nullptr;   // chi | charge | segoff | lam | entropy | gam
+  void* snap = nullptr;
+  size_t state_bytes = 0;
+  MpoDev dev{};
+  int* d_err = nullptr;
+  int* d_chicap = nullptr;
+  std::vector<int> chicap;
+  // gate workspace
+  void* ws_buf = nullptr;
+  SlotWS ws{};
+  int nslots = 0;
+  // single-gate helpers
+  GateDesc* d_gate1 = nullptr;
+  double* d_disc1 = nullptr;
+  // observables
+  double2* d_obs_scratch = nullptr;
+  double* d_obs_out = nullptr;
+  // pinned host staging for mpo_sweep_mesh (gate descriptors in, discarded weights out)
+  void* pin = nullptr;
+  size_t pin_bytes = 0;
+  int poisoned = 0;
+};
+
+struct mpo_plan_s {
+  mpo_handle h = nullptr;
+  std::vector<int> layer_off, layer_cnt;
+  GateDesc* d_gates = nullptr;
+  double* d_disc = nullptr;
+  double* d_phase = nullptr;
+  int ngates = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+mpo_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MPO_OK;
+  if (e == cudaErrorMemoryAllocation) return MPO_ERR_OOM;
+  return MPO_ERR_CUDA;
+}
+
+#define CK(call)                                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      return cuda_status(e_);                          \
+    }                                                  \
+  } while (0)
+
+// number of configurations of k modes (photons 0..d-1 each) with total exactly x
+double n_configs(int k, int x, int d) {
+  std::vector<double> cur(x + 1, 0.0), nxt(x + 1);
+  cur[0] = 1.0;
+  for (int m = 0; m < k; ++m) {
+    std::fill(nxt.begin(), nxt.end(), 0.0);
+    for (int t = 0; t <= x; ++t)
+      for (int n = 0; n < d && n <= t; ++n) nxt[t] += cur[t - n];
+    cur.swap(nxt);
+  }
+  return cur[x];
+}
+
+// largest exact Schmidt rank over the bonds of the capped augmented state
+long long exact_rank_bound(int M, int d, int ncap) {
+  double best = 0.0;
+  for (int b = 0; b <= M; ++b) {
+    double tot = 0.0;
+    for (int c = 0; c <= ncap; ++c)
+      for (int cb = 0; cb <= ncap; ++cb) {
+        double R = n_configs(M - b, c, d) * n_configs(M - b, cb, d);
+        double L1 = 0.0, L2 = 0.0;
+        for (int x = 0; x <= ncap - c; ++x) L1 += n_configs(b, x, d);
+        for (int x = 0; x <= ncap - cb; ++x) L2 += n_configs(b, x, d);
+        tot += std::min(R, L1 * L2);
+      }
+    best = std::max(best, tot);
+  }
+  return best > 1e9 ? (long long)1e9 : (long long)best;
+}
+
+mpo_status poll_error(mpo_handle h) {
+  int err[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err[0] != 0) {
+    h->poisoned = 1;
+    fprintf(stderr, "gbs_mpo: device error %d (info %d)\n", err[0], err[1]);
+    return (mpo_status)err[0];
+  }
+  return MPO_OK;
+}
+
+mpo_status ensure_slots(mpo_handle h, int need) {
+  if (need <= h->nslots) return MPO_OK;
+  if (h->ws_buf) { CK(cudaStreamSynchronize(h->stream)); CK(cudaFree(h->ws_buf)); h->ws_buf = nullptr; }
+  SlotWS w{};
+  w.Pc = h->Pc; w.D = h->D; w.P = h->P;
+  const long long D = h->D;
+  w.capRC = (long long)h->Pc * D;
+  w.capCand = (long long)h->Pc * D;
+  w.capTheta = (long long)h->Pc * D * D;
+  // per-slot budget for Theta/G/V (3 complex arrays): 2 GiB
+  const long long budget = (2ll << 30) / (3 * (long long)sizeof(double2));
+  if (w.capTheta > budget) w.capTheta = budget;
+  w.capGram = w.capTheta;
+  const int S = need;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  size_t o_blk = take((size_t)S * BF_NFIELDS * (w.Pc + 1) * sizeof(int));
+  size_t o_scal = take((size_t)S * SS_NFIELDS * sizeof(int));
+  size_t o_ro = take((size_t)S * w.Pc * w.P * sizeof(int));
+  size_t o_co = take((size_t)S * w.Pc * w.P * sizeof(int));
+  size_t o_rm = take((size_t)S * w.capRC * sizeof(int));
+  size_t o_cm = take((size_t)S * w.capRC * sizeof(int));
+  size_t o_fk = take((size_t)S * MPO_FOCK_MAX * sizeof(double2));
+  size_t o_th = take((size_t)S * w.capTheta * sizeof(double2));
+  size_t o_g = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_v = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_sv = take((size_t)S * w.capCand * sizeof(double));
+  size_t o_pm = take((size_t)S * w.capCand * sizeof(int));
+  size_t o_ds = take((size_t)S * 4 * sizeof(double));
+  size_t o_or = take((size_t)S * w.capCand * 2 * sizeof(int));
+  void* buf = nullptr;
+  CK(cudaMalloc(&buf, off));
+  CK(cudaMemsetAsync(buf, 0, off, h->stream));
+  char* b = (char*)buf;
+  w.blk = (int*)(b + o_blk); w.scal = (int*)(b + o_scal); w.rowoff = (int*)(b + o_ro);
+  w.coloff = (int*)(b + o_co); w.rowmap = (int*)(b + o_rm); w.colmap = (int*)(b + o_cm);
+  w.fock = (double2*)(b + o_fk); w.theta = (double2*)(b + o_th); w.G = (double2*)(b + o_g);
+  w.V = (double2*)(b + o_v); w.sval = (double*)(b + o_sv); w.perm = (int*)(b + o_pm);
+  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or);
+  h->ws_buf = buf;
+  h->ws = w;
+  h->nslots = S;
+  return MPO_OK;
+}
+
+// Greedy layering per instance; layer l of the plan holds every instance's layer l.
+mpo_status build_schedule(mpo_handle h, const int* n_gates, const int* k, const double* theta,
+                          const double* phi, std::vector<GateDesc>& out, std::vector<int>& loff,
+                          std::vector<int>& lcnt, int& total) {
+  total = 0;
+  for (int i = 0; i < h->B; ++i) {
+    if (n_gates[i] < 0) return MPO_ERR_ARG;
+    total += n_gates[i];
+  }
+  std::vector<std::vector<GateDesc>> layers;
+  int g0 = 0;
+  for (int i = 0; i < h->B; ++i) {
+    std::vector<int> last(h->M, -1);
+    for (int t = 0; t < n_gates[i]; ++t) {
+      const int gi = g0 + t;
+      const int kk = k[gi];
+      if (kk < 0 || kk > h->M - 2 || !std::isfinite(theta[gi]) || !std::isfinite(phi[gi])) return MPO_ERR_ARG;
+      const int l = std::max(last[kk], last[kk + 1]) + 1;
+      last[kk] = last[kk + 1] = l;
+      if ((int)layers.size() <= l) layers.resize(l + 1);
+      GateDesc gd{};
+      gd.inst = i; gd.j = kk; gd.out = gi; gd.theta = theta[gi]; gd.phi = phi[gi];
+      layers[l].push_back(gd);
+    }
+    g0 += n_gates[i];
+  }
+  out.clear(); loff.clear(); lcnt.clear();
+  for (auto& L : layers) {
+    loff.push_back((int)out.size());
+    lcnt.push_back((int)L.size());
+    out.insert(out.end(), L.begin(), L.end());
+  }
+  return MPO_OK;
+}
+
+mpo_status run_layers(mpo_handle h, const GateDesc* d_gates, const std::vector<int>& loff,
+                      const std::vector<int>& lcnt, double* d_disc, const double* d_phase, int* launches) {
+  for (size_t l = 0; l < loff.size(); ++l) {
+    launch_layer(h->dev, h->ws, d_gates + loff[l], lcnt[l], d_disc, h->prec, h->stream, launches);
+    CK(cudaGetLastError());
+  }
+  if (d_phase) {
+    launch_phases(h->dev, d_phase, h->stream);
+    if (launches) *launches += 1;
+    CK(cudaGetLastError());
+  }
+  return MPO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpo_status_string(mpo_status s) {
+  switch (s) {
+    case MPO_OK: return "ok";
+    case MPO_ERR_ARG: return "invalid argument";
+    case MPO_ERR_OOM: return "device out of memory";
+    case MPO_ERR_CUDA: return "CUDA runtime error";
+    case MPO_ERR_NUMERIC: return "numerical failure (eigensolver sweep cap or non-finite value)";
+    case MPO_ERR_TIMEOUT: return "bounded device wait ran out";
+    case MPO_ERR_CAPACITY: return "per-gate workspace capacity exceeded";
+    case MPO_ERR_INTERNAL: return "device consistency check failed";
+    case MPO_ERR_POISONED: return "handle poisoned by an earlier device error";
+    case MPO_ERR_NOT_BUILT: return "CUDA library unavailable";
+  }
+  return "unknown status";
+}
+
+mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const double* r,
+                                   const double* eta) {
+  if (!out || !p || !r || !eta) return MPO_ERR_ARG;
+  *out = nullptr;
+  const int M = p->M, d = p->d, B = p->batch;
+  const int ncap = p->n_cap <= 0 ? d - 1 : p->n_cap;
+  if (M < 2 || M > 256 || d < 2 || d > MPO_D_LOCAL_MAX || B < 1 || ncap > d - 1 || ncap > MPO_NCAP_MAX)
+    return MPO_ERR_ARG;
+  if (p->prec != MPO_FP64 && p->prec != MPO_MIXED_TF32 && p->prec != MPO_MIXED_BF16) return MPO_ERR_ARG;
+  for (long long i = 0; i < (long long)B * M; ++i) {
+    if (!(r[i] >= 0.0 && r[i] <= 3.0) || !(eta[i] >= 0.0 && eta[i] <= 1.0)) return MPO_ERR_ARG;
+  }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return MPO_ERR_NOT_BUILT;
+  mpo_ctx* h = new (std::nothrow) mpo_ctx();
+  if (!h) return MPO_ERR_OOM;
+  h->M = M; h->d = d; h->ncap = ncap; h->B = B;
+  h->P = (ncap + 1) * (ncap + 1);
+  h->Pc = (ncap + 1) * (ncap + 2) / 2;
+  h->prec = p->prec;
+  h->chicap.resize(B);
+  long long D = h->P;
+  bool any_nocap = false;
+  for (int i = 0; i < B; ++i) {
+    int c = p->chi_max ? p->chi_max[i] : 0;
+    h->chicap[i] = c;
+    if (c <= 0) any_nocap = true;
+    else D = std::max<long long>(D, c);
+  }
+  if (any_nocap) D = std::max<long long>(D, exact_rank_bound(M, d, ncap));
+  D = (D + 7) / 8 * 8;
+  if (D > 4096) { delete h; return MPO_ERR_ARG; }
+  h->D = (int)D;
+  if (p->cuda_stream) h->stream = (cudaStream_t)p->cuda_stream;
+  else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return MPO_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  // state layout
+  const long long nb = (long long)B * (M + 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  size_t o_chi = take(nb * sizeof(int));
+  size_t o_ch = take(nb * D * sizeof(int));
+  size_t o_seg = take(nb * (h->P + 1) * sizeof(int));
+  size_t o_lam = take(nb * D * sizeof(double));
+  size_t o_ent = take(nb * sizeof(double));
+  size_t o_gam = take((size_t)B * M * D * D * sizeof(double2));
+  h->state_bytes = off;
+  mpo_status st = MPO_OK;
+  auto fail = [&](mpo_status s) { mpo_destroy(h); return s; };
+  if (cudaMalloc(&h->state, off) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&h->snap, off) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMemsetAsync(h->state, 0, off, h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  char* sb = (char*)h->state;
+  MpoDev& dv = h->dev;
+  dv.B = B; dv.M = M; dv.ncap = ncap; dv.P = h->P; dv.D = (int)D;
+  dv.chi = (int*)(sb + o_chi); dv.charge = (int*)(sb + o_ch); dv.segoff = (int*)(sb + o_seg);
+  dv.lam = (double*)(sb + o_lam); dv.entropy = (double*)(sb + o_ent); dv.gam = (double2*)(sb + o_gam);
+  if (cudaMalloc(&h->d_err, 4 * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&h->d_chicap, B * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  dv.err = h->d_err; dv.chi_cap = h->d_chicap;
+  if (cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  if (cudaMemcpyAsync(h->d_chicap, h->chicap.data(), B * sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return fail(MPO_ERR_CUDA);
+  // init scratch
+  const long long per = (long long)(M + 1) * h->P * 3 + (long long)M * h->P * 2 + 64;
+  double* d_scr = nullptr; double* d_re = nullptr;
+  if (cudaMalloc(&d_scr, per * B * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&d_re, 2ll * B * M * sizeof(double)) != cudaSuccess) { cudaFree(d_scr); return fail(MPO_ERR_OOM); }
+  cudaMemcpyAsync(d_re, r, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(d_re + (size_t)B * M, eta, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  launch_init(h->dev, d_re, d_re + (size_t)B * M, d, d_scr, h->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_scr); cudaFree(d_re);
+  if (e != cudaSuccess) return fail(cuda_status(e));
+  if (gate_module_init() != cudaSuccess) return fail(MPO_ERR_CUDA);
+  st = poll_error(h);
+  if (st != MPO_OK) return fail(st);
+  if (cudaMemcpyAsync(h->snap, h->state, off, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+    return fail(MPO_ERR_CUDA);
+  // helpers
+  if (cudaMalloc(&h->d_gate1, sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&h->d_disc1, sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&h->d_obs_scratch, 2ll * B * (M + 1) * D * sizeof(double2)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&h->d_obs_out, (size_t)B * (1 + 2 * M + M + 1) * sizeof(double)) != cudaSuccess)
+    return fail(MPO_ERR_OOM);
+  st = ensure_slots(h, 1);
+  if (st != MPO_OK) return fail(st);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  *out = h;
+  return MPO_OK;
+}
+
+mpo_status mpo_reset(mpo_handle h) {
+  if (!h) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  CK(cudaMemcpyAsync(h->state, h->snap, h->state_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  return MPO_OK;
+}
+
+mpo_status mpo_apply_bs(mpo_handle h, int inst, int k, double theta, double phi, double* discarded_weight) {
+  if (!h) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  if (inst < 0 || inst >= h->B || k < 0 || k > h->M - 2 || !std::isfinite(theta) || !std::isfinite(phi))
+    return MPO_ERR_ARG;
+  GateDesc gd{};
+  gd.inst = inst; gd.j = k; gd.out = 0; gd.theta = theta; gd.phi = phi;
+  CK(cudaMemcpyAsync(h->d_gate1, &gd, sizeof(gd), cudaMemcpyHostToDevice, h->stream));
+  launch_layer(h->dev, h->ws, h->d_gate1, 1, h->d_disc1, h->prec, h->stream, nullptr);
+  CK(cudaGetLastError());
+  if (discarded_weight) {
+    CK(cudaMemcpyAsync(discarded_weight, h->d_disc1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return poll_error(h);
+  }
+  CK(cudaStreamSynchronize(h->stream));  // the host GateDesc must outlive the copy
+  return MPO_OK;
+}
+
+mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k, const double* theta,
+                          const double* phi, const double* final_phase, double* discarded) {
+  if (!h || !n_gates || !k || !theta || !phi) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  std::vector<GateDesc> gates;
+  std::vector<int> loff, lcnt;
+  int total = 0;
+  mpo_status st = build_schedule(h, n_gates, k, theta, phi, gates, loff, lcnt, total);
+  if (st != MPO_OK) return st;
+  int maxl = 1;
+  for (int c : lcnt) maxl = std::max(maxl, c);
+  st = ensure_slots(h, maxl);
+  if (st != MPO_OK) return st;
+  GateDesc* d_g = nullptr; double* d_disc = nullptr; double* d_ph = nullptr;
+  const size_t ng = std::max<size_t>(1, gates.size());
+  const size_t nph = final_phase ? (size_t)h->B * h->M : 0;
+  // pinned staging: [gates | phases | discarded]
+  const size_t need = align_up(ng * sizeof(GateDesc)) + align_up(nph * sizeof(double) + 8) +
+                      align_up(std::max(1, total) * sizeof(double));
+  if (need > h->pin_bytes) {
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->pin) cudaFreeHost(h->pin);
+    h->pin = nullptr; h->pin_bytes = 0;
+    CK(cudaHostAlloc(&h->pin, need, cudaHostAllocDefault));
+    h->pin_bytes = need;
+  }
+  char* pb = (char*)h->pin;
+  GateDesc* hg = (GateDesc*)pb;
+  double* hph = (double*)(pb + align_up(ng * sizeof(GateDesc)));
+  double* hdisc = (double*)(pb + align_up(ng * sizeof(GateDesc)) + align_up(nph * sizeof(double) + 8));
+  if (!gates.empty()) std::memcpy(hg, gates.data(), gates.size() * sizeof(GateDesc));
+  if (nph) std::memcpy(hph, final_phase, nph * sizeof(double));
+  CK(cudaMallocAsync((void**)&d_g, ng * sizeof(GateDesc), h->stream));
+  CK(cudaMallocAsync((void**)&d_disc, std::max(1, total) * sizeof(double), h->stream));
+  if (nph) CK(cudaMallocAsync((void**)&d_ph, nph * sizeof(double), h->stream));
+  if (!gates.empty())
+    CK(cudaMemcpyAsync(d_g, hg, gates.size() * sizeof(GateDesc), cudaMemcpyHostToDevice, h->stream));
+  if (nph) CK(cudaMemcpyAsync(d_ph, hph, nph * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  st = run_layers(h, d_g, loff, lcnt, d_disc, d_ph, nullptr);
+  if (st == MPO_OK && discarded && total > 0)
+    st = cuda_status(cudaMemcpyAsync(hdisc, d_disc, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  cudaFreeAsync(d_g, h->stream);
+  cudaFreeAsync(d_disc, h->stream);
+  if (d_ph) cudaFreeAsync(d_ph, h->stream);
+  if (st != MPO_OK) return st;
+  st = poll_error(h);
+  if (st == MPO_OK && discarded && total > 0) std::memcpy(discarded, hdisc, total * sizeof(double));
+  return st;
+}
+
+mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k, const double* theta,
+                         const double* phi, const double* final_phase, mpo_plan* out) {
+  if (!h || !n_gates || !k || !theta || !phi || !out) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  *out = nullptr;
+  mpo_plan_s* pl = new (std::nothrow) mpo_plan_s();
+  if (!pl) return MPO_ERR_OOM;
+  pl->h = h;
+  std::vector<GateDesc> gates;
+  int total = 0;
+  mpo_status st = build_schedule(h, n_gates, k, theta, phi, gates, pl->layer_off, pl->layer_cnt, total);
+  if (st != MPO_OK) { delete pl; return st; }
+  pl->ngates = total;
+  int maxl = 1;
+  for (int c : pl->layer_cnt) maxl = std::max(maxl, c);
+  st = ensure_slots(h, maxl);
+  if (st != MPO_OK) { delete pl; return st; }
+  auto fail = [&](mpo_status s) { mpo_plan_destroy(pl); return s; };
+  if (cudaMalloc(&pl->d_gates, std::max<size_t>(1, gates.size()) * sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (cudaMalloc(&pl->d_disc, std::max(1, total) * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (!gates.empty() && cudaMemcpy(pl->d_gates, gates.data(), gates.size() * sizeof(GateDesc),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MPO_ERR_CUDA);
+  if (final_phase) {
+    if (cudaMalloc(&pl->d_phase, (size_t)h->B * h->M * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+    if (cudaMemcpy(pl->d_phase, final_phase, (size_t)h->B * h->M * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(MPO_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  int launches = 0;
+  st = run_layers(h, pl->d_gates, pl->layer_off, pl->layer_cnt, pl->d_disc, pl->d_phase, &launches);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (st != MPO_OK) { if (graph) cudaGraphDestroy(graph); return fail(st); }
+  if (e != cudaSuccess) return fail(MPO_ERR_CUDA);
+  pl->graph = graph;
+  if (cudaGraphInstantiate(&pl->exec, graph, 0) != cudaSuccess) return fail(MPO_ERR_CUDA);
+  pl->launches = launches;
+  *out = pl;
+  return MPO_OK;
+}
+
+mpo_status mpo_plan_run(mpo_plan p) {
+  if (!p || !p->h) return MPO_ERR_ARG;
+  if (p->h->poisoned) return MPO_ERR_POISONED;
+  CK(cudaGraphLaunch(p->exec, p->h->stream));
+  return MPO_OK;
+}
+
+mpo_status mpo_plan_discarded(mpo_plan p, double* discarded) {
+  if (!p || !discarded) return MPO_ERR_ARG;
+  if (p->ngates > 0)
+    CK(cudaMemcpyAsync(discarded, p->d_disc, p->ngates * sizeof(double), cudaMemcpyDeviceToHost, p->h->stream));
+  return poll_error(p->h);
+}
+
+int mpo_plan_launches(mpo_plan p) { return p ? p->launches : 0; }
+
+mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, double* stage_flops) {
+  if (!p || !p->h) return MPO_ERR_ARG;
+  mpo_handle h = p->h;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  const int L = (int)p->layer_off.size();
+  std::vector<cudaEvent_t> ev((size_t)L * 7 + 2);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  unsigned long long* d_ctr = nullptr;
+  CK(cudaMallocAsync((void**)&d_ctr, CTR_N * sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(d_ctr, 0, CTR_N * sizeof(unsigned long long), h->stream));
+  MpoDev dv = h->dev;
+  dv.ctr = d_ctr;
+  for (int l = 0; l < L; ++l)
+    launch_layer(dv, h->ws, p->d_gates + p->layer_off[l], p->layer_cnt[l], p->d_disc, h->prec,
+                 h->stream, nullptr, ev.data() + (size_t)l * 7);
+  CK(cudaEventRecord(ev[(size_t)L * 7], h->stream));
+  if (p->d_phase) launch_phases(h->dev, p->d_phase, h->stream);
+  CK(cudaEventRecord(ev[(size_t)L * 7 + 1], h->stream));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  double ms[MPO_NSTAGES] = {0};
+  for (int l = 0; l < L; ++l)
+    for (int st = 0; st < 6; ++st) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[(size_t)l * 7 + st], ev[(size_t)l * 7 + st + 1]));
+      ms[st] += t;
+    }
+  float tp = 0.f;
+  CK(cudaEventElapsedTime(&tp, ev[(size_t)L * 7], ev[(size_t)L * 7 + 1]));
+  ms[6] = tp;
+  for (auto& e : ev) cudaEventDestroy(e);
+  unsigned long long ctr[CTR_N];
+  CK(cudaMemcpyAsync(ctr, d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFreeAsync(d_ctr, h->stream);
+  // stage order: setup, theta, gram, eig, select, resplit, phases
+  const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], (double)ctr[CTR_EIG],
+                                  0.0, (double)ctr[CTR_RESPLIT], 0.0};
+  for (int st = 0; st < MPO_NSTAGES; ++st) {
+    if (stage_ms) stage_ms[st] = ms[st];
+    if (stage_launches) stage_launches[st] = st < 6 ? L : (p->d_phase ? 1 : 0);
+    if (stage_flops) stage_flops[st] = fl[st];
+  }
+  return poll_error(h);
+}
+
+void mpo_plan_destroy(mpo_plan p) {
+  if (!p) return;
+  if (p->h && p->h->stream) cudaStreamSynchronize(p->h->stream);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->d_gates) cudaFree(p->d_gates);
+  if (p->d_disc) cudaFree(p->d_disc);
+  if (p->d_phase) cudaFree(p->d_phase);
+  delete p;
+}
+
+mpo_status mpo_observables(mpo_handle h, double* trace, double* n_mean, double* n2_mean, int normalize_by_trace) {
+  if (!h) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  launch_observables(h->dev, h->d_obs_scratch, h->d_obs_out, h->stream);
+  CK(cudaGetLastError());
+  const int M = h->M, per = 1 + 2 * M + M + 1;
+  std::vector<double> buf((size_t)h->B * per);
+  CK(cudaMemcpyAsync(buf.data(), h->d_obs_out, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  mpo_status st = poll_error(h);
+  if (st != MPO_OK) return st;
+  for (int i = 0; i < h->B; ++i) {
+    const double* o = buf.data() + (size_t)i * per;
+    const double tr = o[0];
+    const double sc = normalize_by_trace ? 1.0 / tr : 1.0;
+    if (trace) trace[i] = tr;
+    for (int j = 0; j < M; ++j) {
+      if (n_mean) n_mean[(size_t)i * M + j] = o[1 + j] * sc;
+      if (n2_mean) n2_mean[(size_t)i * M + j] = o[1 + M + j] * sc;
+    }
+  }
+  return MPO_OK;
+}
+
+mpo_status mpo_operator_entropy(mpo_handle h, double* S, double* purity, double* S_max_running) {
+  if (!h) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  const int M = h->M;
+  std::vector<double> ent((size_t)h->B * (M + 1));
+  CK(cudaMemcpyAsync(ent.data(), h->dev.entropy, ent.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<double> buf;
+  if (purity) {
+    launch_observables(h->dev, h->d_obs_scratch, h->d_obs_out, h->stream);
+    CK(cudaGetLastError());
+    const int per = 1 + 2 * M + M + 1;
+    buf.resize((size_t)h->B * per);
+    CK(cudaMemcpyAsync(buf.data(), h->d_obs_out, buf.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  mpo_status st = poll_error(h);
+  if (st != MPO_OK) return st;
+  for (int i = 0; i < h->B; ++i) {
+    double mx = 0.0;
+    for (int b = 0; b <= M; ++b) {
+      const double v = ent[(size_t)i * (M + 1) + b];
+      if (S) S[(size_t)i * (M + 1) + b] = v;
+      mx = std::max(mx, v);
+      if (purity) purity[(size_t)i * (M + 1) + b] = buf[(size_t)i * (1 + 3 * M + 1) + 1 + 2 * M + b];
+    }
+    if (S_max_running) S_max_running[i] = mx;
+  }
+  return MPO_OK;
+}
+
+mpo_status mpo_get_bonds(mpo_handle h, int inst, int ld, int* chi, double* lam, int* charge) {
+  if (!h || inst < 0 || inst >= h->B) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  const int M = h->M, D = h->D;
+  std::vector<int> c(M + 1);
+  CK(cudaMemcpyAsync(c.data(), h->dev.chi + (size_t)inst * (M + 1), (M + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int mx = 0;
+  for (int v : c) mx = std::max(mx, v);
+  if ((lam || charge) && ld < mx) return MPO_ERR_ARG;
+  if (chi) std::memcpy(chi, c.data(), (M + 1) * sizeof(int));
+  std::vector<double> l((size_t)(M + 1) * D);
+  std::vector<int> ch((size_t)(M + 1) * D);
+  CK(cudaMemcpyAsync(l.data(), h->dev.lam + (size_t)inst * (M + 1) * D, l.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(ch.data(), h->dev.charge + (size_t)inst * (M + 1) * D, ch.size() * sizeof(int),
+                     cudaMemcpyDeviceToHost, h->stream));
+  mpo_status st = poll_error(h);
+  if (st != MPO_OK) return st;
+  for (int b = 0; b <= M; ++b)
+    for (int i = 0; i < c[b]; ++i) {
+      if (lam) lam[(size_t)b * ld + i] = l[(size_t)b * D + i];
+      if (charge) {
+        const int p = ch[(size_t)b * D + i];
+        charge[((size_t)b * ld + i) * 2] = pair_c(p, h->ncap);
+        charge[((size_t)b * ld + i) * 2 + 1] = pair_cb(p, h->ncap);
+      }
+    }
+  return MPO_OK;
+}
+
+int mpo_bond_capacity(mpo_handle h) { return h ? h->D : 0; }
+
+mpo_status mpo_sync(mpo_handle h) {
+  if (!h) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  return poll_error(h);
+}
+
+void mpo_destroy(mpo_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->state) cudaFree(h->state);
+  if (h->snap) cudaFree(h->snap);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_chicap) cudaFree(h->d_chicap);
+  if (h->ws_buf) cudaFree(h->ws_buf);
+  if (h->d_gate1) cudaFree(h->d_gate1);
+  if (h->d_disc1) cudaFree(h->d_disc1);
+  if (h->d_obs_scratch) cudaFree(h->d_obs_scratch);
+  if (h->d_obs_out) cudaFree(h->d_obs_out);
+  if (h->pin) cudaFreeHost(h->pin);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+"""Python binding of libgbsmpo.so (argument marshalling only; every step runs in CUDA).
+
+Names follow the C ABI of include/gbs_mpo.h.  The library is loaded from this
+package directory; if it is missing or cannot be loaded the binding raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbsmpo.so")
+
+MPO_FP64, MPO_MIXED_TF32, MPO_MIXED_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": MPO_FP64, "mixed_tf32": MPO_MIXED_TF32, "mixed_bf16": MPO_MIXED_BF16}
+
+# every symbol declared in include/gbs_mpo.h
+EXPORTS = [
+    "mpo_init_lossy_squeezed", "mpo_reset", "mpo_apply_bs", "mpo_sweep_mesh", "mpo_plan_mesh",
+    "mpo_plan_run", "mpo_plan_discarded", "mpo_plan_launches", "mpo_plan_profile",
+    "mpo_plan_destroy",
+    "mpo_observables", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
+    "mpo_sync", "mpo_destroy", "mpo_status_string",
+]
+
+
+class MPOError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().mpo_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("d", ctypes.c_int), ("n_cap", ctypes.c_int),
+                ("batch", ctypes.c_int), ("prec", ctypes.c_int),
+                ("chi_max", ctypes.POINTER(ctypes.c_int)), ("cuda_stream", ctypes.c_void_p)]
+
+
+_LIB = None
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libgbsmpo.so and declare its signatures.  Raises if it is absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libgbsmpo.so not built at {path}: call __graft_entry__.build() "
+                           "or python -m paper_2301_12814_gb300.build")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "mpo_init_lossy_squeezed": (_i, [ctypes.POINTER(_p), ctypes.POINTER(_Params), _dp, _dp]),
+        "mpo_reset": (_i, [_p]),
+        "mpo_apply_bs": (_i, [_p, _i, _i, ctypes.c_double, ctypes.c_double, _dp]),
+        "mpo_sweep_mesh": (_i, [_p, _ip, _ip, _dp, _dp, _dp, _dp]),
+        "mpo_plan_mesh": (_i, [_p, _ip, _ip, _dp, _dp, _dp, ctypes.POINTER(_p)]),
+        "mpo_plan_run": (_i, [_p]),
+        "mpo_plan_discarded": (_i, [_p, _dp]),
+        "mpo_plan_launches": (_i, [_p]),
+        "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp]),
+        "mpo_plan_destroy": (None, [_p]),
+        "mpo_observables": (_i, [_p, _dp, _dp, _dp, _i]),
+        "mpo_operator_entropy": (_i, [_p, _dp, _dp, _dp]),
+        "mpo_get_bonds": (_i, [_p, _i, _i, _ip, _dp, _ip]),
+        "mpo_bond_capacity": (_i, [_p]),
+        "mpo_sync": (_i, [_p]),
+        "mpo_destroy": (None, [_p]),
+        "mpo_status_string": (ctypes.c_char_p, [_i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _lib() -> ctypes.CDLL:
+    return load_library()
+
+
+def _d(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _ip_of(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_ip)
+
+
+def _check(st: int, where: str) -> None:
+    if st != 0:
+        raise MPOError(st, where)
+
+
+class Plan:
+    """A mesh uploaded once and captured in a CUDA graph (mpo_plan_*)."""
+
+    def __init__(self, owner: "MPO", n_gates, k, theta, phi, final_phase):
+        self._owner = owner
+        self.n_total = int(np.sum(n_gates))
+        h = _p()
+        _check(_lib().mpo_plan_mesh(owner._h, _ip_of(n_gates), _ip_of(k), _d(theta), _d(phi),
+                                    _d(final_phase), ctypes.byref(h)), "mpo_plan_mesh")
+        self._h = h
+        self.launches = int(_lib().mpo_plan_launches(h))
+
+    def run(self) -> None:
+        _check(_lib().mpo_plan_run(self._h), "mpo_plan_run")
+
+    def discarded(self) -> np.ndarray:
+        out = np.zeros(max(self.n_total, 1))
+        _check(_lib().mpo_plan_discarded(self._h, _d(out)), "mpo_plan_discarded")
+        return out[:self.n_total]
+
+    STAGES = ("setup", "theta", "gram", "eig", "select", "resplit", "phases")
+
+    def profile(self):
+        """One instrumented replay: {stage: (ms, launches, flops)}."""
+        ms = np.zeros(7); nl = np.zeros(7, dtype=np.int32); fl = np.zeros(7)
+        _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl)), "mpo_plan_profile")
+        return {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib().mpo_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MPO:
+    """A batch of lossy-GBS U(1) MPOs on the GPU (mpo_init_lossy_squeezed and friends)."""
+
+    def __init__(self, M: int, d: int, r, eta, chi_max=None, batch: int = 1,
+                 n_cap: Optional[int] = None, precision: str = "fp64", stream=None):
+        lib = _lib()
+        self.M, self.d, self.batch = int(M), int(d), int(batch)
+        r = np.ascontiguousarray(np.broadcast_to(np.asarray(r, dtype=np.float64), (batch, M)))
+        eta = np.ascontiguousarray(np.broadcast_to(np.asarray(eta, dtype=np.float64), (batch, M)))
+        if chi_max is None:
+            chis = np.zeros(batch, dtype=np.int32)
+        else:
+            chis = np.ascontiguousarray(np.broadcast_to(
+                np.asarray([0 if c is None else c for c in np.atleast_1d(chi_max)], dtype=np.int32),
+                (batch,)))
+        self._chis = chis
+        sp = None
+        if stream is not None:
+            sp = int(getattr(stream, "cuda_stream", stream))
+        prm = _Params(M=self.M, d=self.d, n_cap=0 if n_cap is None else int(n_cap), batch=self.batch,
+                      prec=PRECISIONS[precision], chi_max=_ip_of(chis), cuda_stream=sp)
+        h = _p()
+        _check(lib.mpo_init_lossy_squeezed(ctypes.byref(h), ctypes.byref(prm), _d(r), _d(eta)),
+               "mpo_init_lossy_squeezed")
+        self._h = h
+        self.D = int(lib.mpo_bond_capacity(h))
+
+    # --------------------------------------------------------------- updates
+    def reset(self) -> None:
+        _check(_lib().mpo_reset(self._h), "mpo_reset")
+
+    def apply_bs(self, k: int, theta: float, phi: float, inst: int = 0,
+                 want_discarded: bool = True) -> Optional[float]:
+        out = np.zeros(1)
+        _check(_lib().mpo_apply_bs(self._h, int(inst), int(k), float(theta), float(phi),
+                                   _d(out) if want_discarded else None), "mpo_apply_bs")
+        return float(out[0]) if want_discarded else None
+
+    @staticmethod
+    def _mesh_arrays(n_gates, k, theta, phi, final_phase):
+        n_gates = np.ascontiguousarray(np.atleast_1d(n_gates), dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        fp = None if final_phase is None else np.ascontiguousarray(final_phase, dtype=np.float64)
+        return n_gates, k, theta, phi, fp
+
+    def sweep_mesh(self, n_gates, k, theta, phi, final_phase=None) -> np.ndarray:
+        n_gates, k, theta, phi, fp = self._mesh_arrays(n_gates, k, theta, phi, final_phase)
+        out = np.zeros(max(int(n_gates.sum()), 1))
+        _check(_lib().mpo_sweep_mesh(self._h, _ip_of(n_gates), _ip_of(k), _d(theta), _d(phi),
+                                     _d(fp), _d(out)), "mpo_sweep_mesh")
+        return out[:int(n_gates.sum())]
+
+    def plan_mesh(self, n_gates, k, theta, phi, final_phase=None) -> Plan:
+        n_gates, k, theta, phi, fp = self._mesh_arrays(n_gates, k, theta, phi, final_phase)
+        return Plan(self, n_gates, k, theta, phi, fp)
+
+    # ----------------------------------------------------------- observables
+    def observables(self, normalize: bool = True):
+        B, M = self.batch, self.M
+        tr = np.zeros(B); n1 = np.zeros(B * M); n2 = np.zeros(B * M)
+        _check(_lib().mpo_observables(self._h, _d(tr), _d(n1), _d(n2), 1 if normalize else 0),
+               "mpo_observables")
+        return tr, n1.reshape(B, M), n2.reshape(B, M)
+
+    def operator_entropy(self):
+        B, M = self.batch, self.M
+        S = np.zeros(B * (M + 1)); pur = np.zeros(B * (M + 1)); smax = np.zeros(B)
+        _check(_lib().mpo_operator_entropy(self._h, _d(S), _d(pur), _d(smax)), "mpo_operator_entropy")
+        return S.reshape(B, M + 1), pur.reshape(B, M + 1), smax
+
+    def bonds(self, inst: int = 0):
+        """(chi[M+1], [lambda_b], [charges_b (chi_b x 2)]) of one instance."""
+        M, ld = self.M, self.D
+        chi = np.zeros(M + 1, dtype=np.int32)
+        lam = np.zeros((M + 1) * ld)
+        ch = np.zeros((M + 1) * ld * 2, dtype=np.int32)
+        _check(_lib().mpo_get_bonds(self._h, int(inst), ld, _ip_of(chi), _d(lam), _ip_of(ch)),
+               "mpo_get_bonds")
+        lam = lam.reshape(M + 1, ld)
+        ch = ch.reshape(M + 1, ld, 2)
+        return chi, [lam[b, :chi[b]].copy() for b in range(M + 1)], \
+            [ch[b, :chi[b]].copy() for b in range(M + 1)]
+
+    def sync(self) -> None:
+        _check(_lib().mpo_sync(self._h), "mpo_sync")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib().mpo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""CPU checks of the C-ABI library: it builds, loads, and exports every symbol that
+include/gbs_mpo.h declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gbs_mpo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpo_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2301_12814_gb300 import build
+    path = build.build()
+    from paper_2301_12814_gb300 import mpo
+    return mpo.load_library(path)
+
+
+def test_header_and_binding_agree():
+    from paper_2301_12814_gb300 import mpo
+    assert _declared() == sorted(mpo.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for s in range(10):
+        assert lib.mpo_status_string(s)
+
+
+def test_host_argument_checks(lib):
+    from paper_2301_12814_gb300 import mpo
+    h = ctypes.c_void_p()
+    r = np.zeros(4); eta = np.ones(4)
+    # null params
+    assert lib.mpo_init_lossy_squeezed(ctypes.byref(h), None, mpo._d(r), mpo._d(eta)) == 1
+    bad = [dict(M=1), dict(d=1), dict(n_cap=9), dict(batch=0), dict(prec=7)]
+    for kw in bad:
+        base = dict(M=4, d=4, n_cap=0, batch=1, prec=0)
+        base.update(kw)
+        prm = mpo._Params(M=base["M"], d=base["d"], n_cap=base["n_cap"], batch=base["batch"],
+                          prec=base["prec"], chi_max=None, cuda_stream=None)
+        assert lib.mpo_init_lossy_squeezed(ctypes.byref(h), ctypes.byref(prm), mpo._d(r),
+                                           mpo._d(eta)) == 1, kw
+    # out-of-range physics parameters
+    prm = mpo._Params(M=4, d=4, n_cap=0, batch=1, prec=0, chi_max=None, cuda_stream=None)
+    assert lib.mpo_init_lossy_squeezed(ctypes.byref(h), ctypes.byref(prm), mpo._d(np.full(4, -1.0)),
+                                       mpo._d(eta)) == 1
+    assert lib.mpo_init_lossy_squeezed(ctypes.byref(h), ctypes.byref(prm), mpo._d(r),
+                                       mpo._d(np.full(4, 1.5))) == 1
+    # null handles
+    assert lib.mpo_apply_bs(None, 0, 0, 0.1, 0.2, None) == 1
+    assert lib.mpo_sync(None) == 1
+    assert lib.mpo_bond_capacity(None) == 0
+
+
+def test_no_gpu_is_reported_not_faked(lib):
+    """Without a GPU the library refuses (MPO_ERR_NOT_BUILT) instead of computing on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2301_12814_gb300 import MPO, MPOError
+    with pytest.raises(MPOError) as ei:
+        MPO(4, 4, [0.5] * 4, [0.5] * 4)
+    assert ei.value.status == 9
