@@ -109,7 +109,9 @@ mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k,
 
 /* Plans: the same mesh as mpo_sweep_mesh, uploaded once and captured in a CUDA
  * graph; mpo_plan_run replays it asynchronously on the handle's stream with the
- * gate list already resident in device memory.  A plan belongs to its handle. */
+ * gate list already resident in device memory.  A plan belongs to its handle:
+ * mpo_destroy(h) destroys every plan of h that is still alive, after which those
+ * plan pointers must not be used. */
 mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k,
                          const double* theta, const double* phi,
                          const double* final_phase, mpo_plan* out);

@@ -44,6 +44,7 @@ struct mpo_ctx {
   // pinned host staging for mpo_sweep_mesh (gate descriptors in, discarded weights out)
   void* pin = nullptr;
   size_t pin_bytes = 0;
+  std::vector<mpo_plan> plans;  // live plans; mpo_destroy destroys them first
   int poisoned = 0;
 };
 
@@ -129,8 +130,8 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
   w.capTheta = (long long)h->Pc * D * D;
-  // per-slot budget for Theta/G/V (3 complex arrays): 2 GiB
-  const long long budget = (2ll << 30) / (3 * (long long)sizeof(double2));
+  // per-slot budget for Theta/W/G/V (4 complex arrays): 2 GiB
+  const long long budget = (2ll << 30) / (4 * (long long)sizeof(double2));
   if (w.capTheta > budget) w.capTheta = budget;
   w.capGram = w.capTheta;
   const int S = need;
@@ -150,6 +151,8 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_pm = take((size_t)S * w.capCand * sizeof(int));
   size_t o_ds = take((size_t)S * 4 * sizeof(double));
   size_t o_or = take((size_t)S * w.capCand * 2 * sizeof(int));
+  size_t o_it = take((size_t)S * w.P * w.P * sizeof(int));
+  size_t o_w = take((size_t)S * w.capTheta * sizeof(double2));
   void* buf = nullptr;
   CK(cudaMalloc(&buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
@@ -158,7 +161,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.coloff = (int*)(b + o_co); w.rowmap = (int*)(b + o_rm); w.colmap = (int*)(b + o_cm);
   w.fock = (double2*)(b + o_fk); w.theta = (double2*)(b + o_th); w.G = (double2*)(b + o_g);
   w.V = (double2*)(b + o_v); w.sval = (double*)(b + o_sv); w.perm = (int*)(b + o_pm);
-  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or);
+  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w);
   h->ws_buf = buf;
   h->ws = w;
   h->nslots = S;
@@ -443,6 +446,7 @@ mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k, const d
   pl->graph = graph;
   if (cudaGraphInstantiate(&pl->exec, graph, 0) != cudaSuccess) return fail(MPO_ERR_CUDA);
   pl->launches = launches;
+  h->plans.push_back(pl);
   *out = pl;
   return MPO_OK;
 }
@@ -511,7 +515,11 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
 
 void mpo_plan_destroy(mpo_plan p) {
   if (!p) return;
-  if (p->h && p->h->stream) cudaStreamSynchronize(p->h->stream);
+  if (p->h) {
+    auto& v = p->h->plans;
+    v.erase(std::remove(v.begin(), v.end(), p), v.end());
+    if (p->h->stream) cudaStreamSynchronize(p->h->stream);
+  }
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->d_gates) cudaFree(p->d_gates);
@@ -614,6 +622,7 @@ mpo_status mpo_sync(mpo_handle h) {
 
 void mpo_destroy(mpo_handle h) {
   if (!h) return;
+  while (!h->plans.empty()) mpo_plan_destroy(h->plans.back());
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->state) cudaFree(h->state);
   if (h->snap) cudaFree(h->snap);

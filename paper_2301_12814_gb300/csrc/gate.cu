@@ -8,37 +8,115 @@
 // singular values over all blocks, and re-split Gamma_j = X / lambda_A,
 // Gamma_{j+1} = Y / lambda_B.
 //
-// GB300 design (differs from the paper's A100 kernels, which were a SIMT GEMM with
-// unitary lookups and a library SVD):
+// GB300 design (differs from the paper's A100 kernels, a SIMT GEMM with unitary
+// lookups over the whole Theta plus a library SVD):
 // * Hermiticity of rho makes Theta(mbar) the ket/bra mirror of Theta(m)
 //   (Theta(mbar)[pi a, pi b] = conj Theta(m)[a, b]).  Only the canonical blocks
 //   m = (c, cbar) with c <= cbar are contracted and factorised; the mirror block's
 //   singular values are bitwise copies and its vectors are conjugated copies.  This
 //   halves the work and makes the mirror spectra exactly degenerate, so the
 //   keep-chi rule never splits a mirror pair.  Self-mirror blocks (c = cbar) are
-//   diagonalised in the basis where the mirror acts as complex conjugation; their
-//   Gram matrix is real there, so the vectors come out mirror-symmetric.
+//   diagonalised in the basis where the mirror acts as complex conjugation: their
+//   Gram matrix is real there (real arithmetic, mirror-symmetric vectors).
+// * The contraction runs per (row segment a, column segment b): the partial product
+//   P_c = Gamma_j[a, c] lambda_c Gamma_{j+1}[c, b] of every old centre segment c is
+//   formed once and mixed into every canonical new centre m between a and b with the
+//   weight u(a, b, c, m).  Eq. `theta` evaluates the same sum per m; factoring P_c out
+//   removes the repeated inner products and all padding of small segments.
 // * The SVD is a Gram matrix (smaller side) plus a parallel-order cyclic Jacobi
-//   eigensolver, one CTA per block; singular values below the Gram accuracy floor
-//   are dropped.
+//   eigensolver, one CTA per block, in two size classes (n <= 32: small CTAs, many
+//   per SM; larger: up to 200 KB of shared memory, global memory beyond that).
+//   Singular values below the Gram accuracy floor are dropped.
 // * The beam-splitter Fock blocks are built on the device by the creation-operator
 //   recurrence U|j, n-j> = (S11 a1^dag + S21 a2^dag) U|j-1, n-j> / sqrt(j).
-// Stages: k_setup (Fock tables, charge bookkeeping) -> k_theta -> k_gram -> k_eig ->
-// k_select (global keep-chi, new bond, lambda, discarded weight, entropy) ->
-// k_resplit (back-multiply, Gamma_j and Gamma_{j+1} including mirror copies).
+// * Precision: R = double (FP64 path) or float (mixed path: contraction, Gram,
+//   eigensolver and back-multiplication in FP32; selection, lambda, discarded weight,
+//   entropy and the stored state in FP64).
+// * The Gram eigenvectors seed a one-sided Jacobi refinement on W = Theta V, which
+//   makes the singular values and vectors accurate relative to s_max (not s_max^2)
+//   and yields both factors, so the re-split is a scaled copy.
+// Stages: k_setup -> k_theta -> k_gram -> k_eig (small, large) -> k_refine ->
+// k_select -> k_resplit.
 #include "mpo_internal.cuh"
 
 namespace {
 
 constexpr int TILE = 16;
-constexpr double GRAM_FLOOR_FP64 = 1e-13;  // drop s^2 <= floor * s_max^2
-constexpr double TIE_REL = 1e-9;           // keep-chi: never split a run closer than this
+constexpr int MCH = 8;        // new-centre charges mixed per pass of the contraction
+constexpr int SMALL_N = 32;   // eigen blocks up to this size use the small-CTA kernel
+constexpr double TIE_REL = 1e-9;
 constexpr int JACOBI_MAX_SWEEPS = 60;
+
+template <typename R> struct Prec;
+// tol_*: two-sided Jacobi on the Gram matrix; os_*: one-sided refinement on
+// W = Theta V; floor: singular values with s^2 <= floor * s_max^2 are dropped (the
+// refined values are accurate to a few ulps of s_max, not of s_max^2).
+template <> struct Prec<double> {
+  typedef double2 C;
+  static constexpr double tol_rel = 1e-15, tol_abs = 1e-18;
+  static constexpr double os_rel = 4e-15, os_abs = 1e-30;
+  static constexpr double floor = 1e-28;
+};
+template <> struct Prec<float> {
+  typedef float2 C;
+  // off-diagonals below ~3 FP32 ulps of the largest diagonal are rounding noise
+  static constexpr float tol_rel = 2e-7f, tol_abs = 2e-7f;
+  static constexpr float os_rel = 2e-6f, os_abs = 1e-13f;
+  static constexpr double floor = 1e-12;
+};
+
+// ---- element helpers for real (self-mirror) and complex Jacobi ----
+__device__ __forceinline__ double re(double x) { return x; }
+__device__ __forceinline__ float re(float x) { return x; }
+__device__ __forceinline__ double re(double2 x) { return x.x; }
+__device__ __forceinline__ float re(float2 x) { return x.x; }
+__device__ __forceinline__ double absv(double x) { return fabs(x); }
+__device__ __forceinline__ float absv(float x) { return fabsf(x); }
+__device__ __forceinline__ double absv(double2 x) { return hypot(x.x, x.y); }
+__device__ __forceinline__ float absv(float2 x) { return hypotf(x.x, x.y); }
+__device__ __forceinline__ double cj(double x) { return x; }
+__device__ __forceinline__ float cj(float x) { return x; }
+__device__ __forceinline__ double2 cj(double2 x) { return make_double2(x.x, -x.y); }
+__device__ __forceinline__ float2 cj(float2 x) { return make_float2(x.x, -x.y); }
+__device__ __forceinline__ double mulv(double a, double b) { return a * b; }
+__device__ __forceinline__ float mulv(float a, float b) { return a * b; }
+__device__ __forceinline__ double2 mulv(double2 a, double2 b) { return cmul(a, b); }
+__device__ __forceinline__ float2 mulv(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double lin(double c, double x, double s, double y) { return c * x + s * y; }
+__device__ __forceinline__ float lin(float c, float x, float s, float y) { return c * x + s * y; }
+__device__ __forceinline__ double2 lin(double c, double2 x, double s, double2 y) {
+  return make_double2(c * x.x + s * y.x, c * x.y + s * y.y);
+}
+__device__ __forceinline__ float2 lin(float c, float2 x, float s, float2 y) {
+  return make_float2(c * x.x + s * y.x, c * x.y + s * y.y);
+}
+template <typename E, typename R> __device__ __forceinline__ E divr(E g, R h);
+template <> __device__ __forceinline__ double divr<double, double>(double g, double h) { return g / h; }
+template <> __device__ __forceinline__ float divr<float, float>(float g, float h) { return g / h; }
+template <> __device__ __forceinline__ double2 divr<double2, double>(double2 g, double h) {
+  return make_double2(g.x / h, g.y / h);
+}
+template <> __device__ __forceinline__ float2 divr<float2, float>(float2 g, float h) {
+  return make_float2(g.x / h, g.y / h);
+}
+template <typename E> __device__ __forceinline__ E unit_e();
+template <> __device__ __forceinline__ double unit_e<double>() { return 1.0; }
+template <> __device__ __forceinline__ float unit_e<float>() { return 1.0f; }
+template <> __device__ __forceinline__ double2 unit_e<double2>() { return make_double2(1.0, 0.0); }
+template <> __device__ __forceinline__ float2 unit_e<float2>() { return make_float2(1.0f, 0.0f); }
+template <typename E> __device__ __forceinline__ E zero_e();
+template <> __device__ __forceinline__ double zero_e<double>() { return 0.0; }
+template <> __device__ __forceinline__ float zero_e<float>() { return 0.0f; }
+template <> __device__ __forceinline__ double2 zero_e<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero_e<float2>() { return make_float2(0.0f, 0.0f); }
+template <typename C> __device__ __forceinline__ C cvt(double2 a);
+template <> __device__ __forceinline__ double2 cvt<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
 struct Slot {
   int* blk; int* scal; int* rowoff; int* coloff; int* rowmap; int* colmap;
-  double2* fock; double2* theta; double2* G; double2* V; double* sval; int* perm;
-  double* dscal; int* order;
+  double2* fock; void* theta; void* G; void* V; double* sval; int* perm;
+  double* dscal; int* order; int* items; void* W;
   int Pc;
   __device__ __forceinline__ int& f(int field, int t) const { return blk[field * (Pc + 1) + t]; }
 };
@@ -60,12 +138,14 @@ __device__ __forceinline__ Slot get_slot(const SlotWS& ws, int s) {
   sl.perm = ws.perm + (long long)s * ws.capCand;
   sl.dscal = ws.dscal + (long long)s * 4;
   sl.order = ws.order + (long long)s * ws.capCand * 2;
+  sl.items = ws.items + (long long)s * ws.P * ws.P;
+  sl.W = ws.W + (long long)s * ws.capTheta;
   return sl;
 }
 
 // largest t in [0, n) with pre[t] <= z  (pre non-decreasing, pre[0] = 0)
 __device__ __forceinline__ int find_block(const int* pre, int n, int z) {
-  int lo = 0, hi = n;  // invariant: pre[lo] <= z, answer in [lo, hi)
+  int lo = 0, hi = n;
   while (hi - lo > 1) {
     int mid = (lo + hi) >> 1;
     if (pre[mid] <= z) lo = mid; else hi = mid;
@@ -73,8 +153,14 @@ __device__ __forceinline__ int find_block(const int* pre, int n, int z) {
   return lo;
 }
 
+// 2-D inclusive prefix count over a (q x q) occupancy table; S has (q+1)^2 entries
+__device__ __forceinline__ int box_count(const int* S, int q, int x0, int x1, int y0, int y1) {
+  const int w = q + 1;
+  return S[(x1 + 1) * w + (y1 + 1)] - S[x0 * w + (y1 + 1)] - S[(x1 + 1) * w + y0] + S[x0 * w + y0];
+}
+
 // ---------------------------------------------------------------- k_setup
-__global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+__global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
   const int s = blockIdx.x;
   const GateDesc g = gates[s];
   Slot sl = get_slot(ws, s);
@@ -82,7 +168,9 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
   const int tid = threadIdx.x, nth = blockDim.x;
   __shared__ int segA[MPO_P_MAX + 1], segC[MPO_P_MAX + 1], segB[MPO_P_MAX + 1];
   __shared__ double2 fk[MPO_FOCK_MAX];
-  __shared__ unsigned char supA[MPO_P_MAX], infB[MPO_P_MAX];
+  __shared__ int preC[(MPO_NCAP_MAX + 2) * (MPO_NCAP_MAX + 2)], preM[(MPO_NCAP_MAX + 2) * (MPO_NCAP_MAX + 2)];
+  __shared__ int preA[(MPO_NCAP_MAX + 2) * (MPO_NCAP_MAX + 2)], preB[(MPO_NCAP_MAX + 2) * (MPO_NCAP_MAX + 2)];
+  __shared__ int cntA[MPO_P_MAX + 1];
   __shared__ int bad;
   if (tid == 0) bad = (g.j < 0 || g.j > M - 2 || g.inst < 0 || g.inst >= st.B);
   __syncthreads();
@@ -118,17 +206,21 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
     __syncthreads();
   }
   for (int e = tid; e < fock_off(ncap + 1); e += nth) sl.fock[e] = fk[e];
-  // dominance tables: supA[x, y] = some A pair (c, cb) present with c >= x, cb >= y
-  //                   infB[x, y] = some B pair present with c <= x, cb <= y
-  for (int p = tid; p < P; p += nth) {
-    int x = pair_c(p, ncap), y = pair_cb(p, ncap);
-    unsigned char sa = 0, ib = 0;
-    for (int a = 0; a < P; ++a) {
-      int ca = pair_c(a, ncap), cba = pair_cb(a, ncap);
-      if (segA[a + 1] > segA[a] && ca >= x && cba >= y) sa = 1;
-      if (segB[a + 1] > segB[a] && ca <= x && cba <= y) ib = 1;
-    }
-    supA[p] = sa; infB[p] = ib;
+  // 2-D prefix counts of the pairs present at A, B and C
+  if (tid == 0) {
+    const int w = q + 1;
+    for (int x = 0; x <= q; ++x)
+      for (int y = 0; y <= q; ++y) {
+        int va = 0, vb = 0, vc = 0;
+        if (x > 0 && y > 0) {
+          const int p = (x - 1) * q + (y - 1);
+          va = segA[p + 1] > segA[p]; vb = segB[p + 1] > segB[p]; vc = segC[p + 1] > segC[p];
+          va += preA[(x - 1) * w + y] + preA[x * w + y - 1] - preA[(x - 1) * w + y - 1];
+          vb += preB[(x - 1) * w + y] + preB[x * w + y - 1] - preB[(x - 1) * w + y - 1];
+          vc += preC[(x - 1) * w + y] + preC[x * w + y - 1] - preC[(x - 1) * w + y - 1];
+        }
+        preA[x * w + y] = va; preB[x * w + y] = vb; preC[x * w + y] = vc;
+      }
   }
   __syncthreads();
   // per canonical block: rows, cols, non-empty test, segment offsets
@@ -145,13 +237,14 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
         sl.coloff[t * P + a] = c; c += nb;
       } else sl.coloff[t * P + a] = -1;
     }
+    // non-empty: some present c, a >= max(c, m), b <= min(c, m)
     bool path = false;
     for (int cc = 0; cc < P && !path; ++cc) {
       if (segC[cc + 1] == segC[cc]) continue;
       int x = pair_c(cc, ncap), y = pair_cb(cc, ncap);
       int hx = x > cm ? x : cm, hy = y > cbm ? y : cbm;
       int lx = x < cm ? x : cm, ly = y < cbm ? y : cbm;
-      if (supA[hx * q + hy] && infB[lx * q + ly]) path = true;
+      if (box_count(preA, q, hx, ncap, hy, ncap) > 0 && box_count(preB, q, 0, lx, 0, ly) > 0) path = true;
     }
     const int gg = (r > 0 && c > 0 && path) ? (r < c ? r : c) : 0;
     sl.f(BF_M, t) = m;
@@ -161,19 +254,31 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
     sl.f(BF_SIDE, t) = (r <= c) ? 0 : 1;
   }
   __syncthreads();
+  // occupancy of non-empty canonical blocks for the item test; offsets and capacities
   if (tid == 0) {
+    const int w = q + 1;
+    for (int x = 0; x <= q; ++x)
+      for (int y = 0; y <= q; ++y) {
+        int v = 0;
+        if (x > 0 && y > 0) {
+          const int cx = x - 1, cy = y - 1;
+          v = (cx <= cy) ? (sl.f(BF_G, canon_index(cx * q + cy, ncap)) > 0) : 0;
+          v += preM[(x - 1) * w + y] + preM[x * w + y - 1] - preM[(x - 1) * w + y - 1];
+        }
+        preM[x * w + y] = v;
+      }
     long long toff = 0, goff = 0, coff = 0, rm = 0, cm2 = 0;
-    int tt = 0, gt = 0;
+    int gt = 0;
     for (int t = 0; t < Pc; ++t) {
       const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), gg = sl.f(BF_G, t);
       sl.f(BF_TOFF, t) = (int)toff; sl.f(BF_GOFF, t) = (int)goff; sl.f(BF_COFF, t) = (int)coff;
       sl.f(BF_RMOFF, t) = (int)rm; sl.f(BF_CMOFF, t) = (int)cm2;
-      sl.f(BF_TT, t) = tt; sl.f(BF_GT, t) = gt;
+      sl.f(BF_GT, t) = gt;
       toff += (long long)r * c; goff += (long long)gg * gg; coff += gg; rm += r; cm2 += c;
-      const int ntr = (r + TILE - 1) / TILE, ntc = (c + TILE - 1) / TILE, ntg = (gg + TILE - 1) / TILE;
-      tt += ntr * ntc; gt += ntg * (ntg + 1) / 2;
+      const int ntg = (gg + TILE - 1) / TILE;
+      gt += ntg * (ntg + 1) / 2;
     }
-    sl.f(BF_TT, Pc) = tt; sl.f(BF_GT, Pc) = gt;
+    sl.f(BF_GT, Pc) = gt;
     sl.f(BF_TOFF, Pc) = (int)toff; sl.f(BF_COFF, Pc) = (int)coff;
     int status = 0;
     if (toff > ws.capTheta || goff > ws.capGram || coff > ws.capCand || rm > ws.capRC || cm2 > ws.capRC) {
@@ -181,12 +286,47 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
       dev_set_error(st.err, DEV_ERR_CAPACITY, 2000);
     }
     sl.scal[SS_NBLK] = Pc;
-    sl.scal[SS_TTILES] = status ? 0 : tt;
     sl.scal[SS_GTILES] = status ? 0 : gt;
+    sl.scal[SS_TTILES] = 0;
     sl.scal[SS_STATUS] = status;
   }
   __syncthreads();
   if (sl.scal[SS_STATUS]) return;
+  // contraction items (a, b): a >= b both present and some non-empty canonical new
+  // centre m with a >= m >= b.  Items without an old centre c between a and b write
+  // the zero sub-block, so every element of every Theta(m) is written each gate.
+  for (int a = tid; a < P; a += nth) {
+    int cnt = 0;
+    if (segA[a + 1] > segA[a]) {
+      const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap);
+      for (int b = 0; b < P; ++b) {
+        if (segB[b + 1] == segB[b]) continue;
+        const int cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+        if (cb > ca || cbb > cba) continue;
+        if (box_count(preM, q, cb, ca, cbb, cba) > 0) ++cnt;
+      }
+    }
+    cntA[a] = cnt;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int a = 0; a < P; ++a) { int c = cntA[a]; cntA[a] = acc; acc += c; }
+    cntA[P] = acc;
+    sl.scal[SS_TTILES] = acc;
+  }
+  __syncthreads();
+  for (int a = tid; a < P; a += nth) {
+    if (segA[a + 1] == segA[a]) continue;
+    int o = cntA[a];
+    const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap);
+    for (int b = 0; b < P; ++b) {
+      if (segB[b + 1] == segB[b]) continue;
+      const int cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+      if (cb > ca || cbb > cba) continue;
+      if (box_count(preM, q, cb, ca, cbb, cba) > 0) sl.items[o++] = a * P + b;
+    }
+  }
   // row / column maps: Theta(m) row i -> bond A index, column -> bond B index
   for (int t = tid; t < Pc; t += nth) {
     if (sl.f(BF_G, t) == 0) continue;
@@ -202,153 +342,165 @@ __global__ void k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates
 }
 
 // ---------------------------------------------------------------- k_theta
-// One 16 x 16 output tile of Theta(m) per iteration; K runs over the segments of the
-// old centre bond C, each weighted by the unitary element u(a, b, c, m).
-template <typename CT>
+// One (row segment a, column segment b) item per iteration, in 16 x 16 element tiles:
+// for every old centre segment c between them, P_c[i][j] = sum_gamma Gamma_j[a_i, gamma]
+// lambda_C[gamma] Gamma_{j+1}[gamma, b_j], then Theta(m)[a_i, b_j] += u(a, b, c, m) P_c
+// for up to MCH canonical new centres m per pass.
+template <typename R>
 __global__ void __launch_bounds__(256) k_theta(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+  typedef typename Prec<R>::C C;
   const int s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
   const GateDesc g = gates[s];
-  const int ncap = st.ncap, q = ncap + 1, P = st.P, M = st.M, D = st.D, Pc = ws.Pc;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  __shared__ double2 fk[MPO_FOCK_MAX];
-  __shared__ int segC[MPO_P_MAX + 1];
-  __shared__ CT As[TILE][TILE + 1], Bs[TILE][TILE + 1];
-  __shared__ int rA[TILE], pA[TILE], cB[TILE], pB[TILE];
-  __shared__ int tpre[MPO_PC_MAX + 1];
-  for (int e = threadIdx.x; e < fock_off(ncap + 1); e += blockDim.x) fk[e] = sl.fock[e];
+  const int ncap = st.ncap, q = ncap + 1, P = st.P, M = st.M, D = st.D;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __shared__ C fk[MPO_FOCK_MAX];
+  __shared__ int segA[MPO_P_MAX + 1], segC[MPO_P_MAX + 1], segB[MPO_P_MAX + 1];
+  __shared__ C As[TILE][TILE + 1], Bs[TILE][TILE + 1];
+  __shared__ int clist[MPO_P_MAX], mlist[MPO_PC_MAX], mro[MPO_PC_MAX], mco[MPO_PC_MAX];
+  __shared__ int ncl, nml;
+  for (int e = tid; e < fock_off(ncap + 1); e += blockDim.x) fk[e] = cvt<C>(sl.fock[e]);
   const long long bA = (long long)g.inst * (M + 1) + g.j, bC = bA + 1, bB = bA + 2;
-  for (int p = threadIdx.x; p <= P; p += blockDim.x) segC[p] = st.segoff[bC * (P + 1) + p];
-  for (int t = threadIdx.x; t <= Pc; t += blockDim.x) tpre[t] = sl.f(BF_TT, t);
-  __syncthreads();
-  const int* chA = st.charge + bA * D;
-  const int* chB = st.charge + bB * D;
+  for (int p = tid; p <= P; p += blockDim.x) {
+    segA[p] = st.segoff[bA * (P + 1) + p];
+    segC[p] = st.segoff[bC * (P + 1) + p];
+    segB[p] = st.segoff[bB * (P + 1) + p];
+  }
   const double* lA = st.lam + bA * D;
   const double* lC = st.lam + bC * D;
   const double* lB = st.lam + bB * D;
   const double2* G1 = st.gam + ((long long)g.inst * M + g.j) * D * D;
   const double2* G2 = G1 + (long long)D * D;
-  const int total = sl.scal[SS_TTILES];
+  C* Th = reinterpret_cast<C*>(sl.theta);
+  const int nitems = sl.scal[SS_TTILES];
   unsigned long long flops = 0;
-  for (int z = blockIdx.x; z < total; z += gridDim.x) {
-    const int t = find_block(tpre, Pc + 1, z);
-    const int r = sl.f(BF_R, t), c = sl.f(BF_C, t);
-    const int m = sl.f(BF_M, t), cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
-    const int ntc = (c + TILE - 1) / TILE;
-    const int local = z - tpre[t];
-    const int i0 = (local / ntc) * TILE, q0 = (local % ntc) * TILE;
-    __syncthreads();
-    if (threadIdx.x < TILE) {
-      int i = i0 + threadIdx.x;
-      int a = (i < r) ? sl.rowmap[sl.f(BF_RMOFF, t) + i] : -1;
-      rA[threadIdx.x] = a; pA[threadIdx.x] = (a >= 0) ? chA[a] : -1;
-    } else if (threadIdx.x < 2 * TILE) {
-      int qq = q0 + threadIdx.x - TILE;
-      int b = (qq < c) ? sl.colmap[sl.f(BF_CMOFF, t) + qq] : -1;
-      cB[threadIdx.x - TILE] = b; pB[threadIdx.x - TILE] = (b >= 0) ? chB[b] : -1;
-    }
-    __syncthreads();
-    const int myA = pA[ty], myB = pB[tx];
-    const int ca = myA >= 0 ? pair_c(myA, ncap) : -1, cba = myA >= 0 ? pair_cb(myA, ncap) : -1;
-    const int cb = myB >= 0 ? pair_c(myB, ncap) : 1 << 20, cbb = myB >= 0 ? pair_cb(myB, ncap) : 1 << 20;
-    // loader roles: row loader uses (ty) row, column loader uses (tx) column
-    const int la = pA[ty];
-    const int lca = la >= 0 ? pair_c(la, ncap) : -1, lcba = la >= 0 ? pair_cb(la, ncap) : -1;
-    const int lb = pB[tx];
-    const int lcb = lb >= 0 ? pair_c(lb, ncap) : 1 << 20, lcbb = lb >= 0 ? pair_cb(lb, ncap) : 1 << 20;
-    double2 acc = make_double2(0.0, 0.0);
-    const bool mine = (i0 + ty < r) && (q0 + tx < c);
-    for (int cc = 0; cc < P; ++cc) {
-      const int k0 = segC[cc], k1 = segC[cc + 1];
-      if (k1 == k0) continue;
-      const int xc = pair_c(cc, ncap), yc = pair_cb(cc, ncap);
-      const bool ok = (ca >= xc && cba >= yc && xc >= cb && yc >= cbb);
-      if (!__syncthreads_or(ok)) continue;
-      const bool rowok = (lca >= xc && lcba >= yc);
-      const bool colok = (xc >= lcb && yc >= lcbb);
-      CT part;
-      part.x = 0; part.y = 0;
-      for (int kb = k0; kb < k1; kb += TILE) {
-        {
-          int kk = kb + tx;
-          double2 v = make_double2(0.0, 0.0);
-          if (rowok && kk < k1) v = G1[(long long)rA[ty] * D + kk];
-          As[ty][tx] = from_d2<CT>(v);
-          int kr = kb + ty;
-          double2 w = make_double2(0.0, 0.0);
-          if (colok && kr < k1) w = cscale(G2[(long long)kr * D + cB[tx]], lC[kr]);
-          Bs[ty][tx] = from_d2<CT>(w);
+  for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
+    const int item = sl.items[z];
+    const int a = item / P, b = item % P;
+    const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+    __syncthreads();  // previous item done with the shared lists (and the loads above)
+    if (tid == 0) {
+      int n1 = 0, n2 = 0;
+      for (int cc = 0; cc < P; ++cc) {
+        if (segC[cc + 1] == segC[cc]) continue;
+        const int x = pair_c(cc, ncap), y = pair_cb(cc, ncap);
+        if (x <= ca && x >= cb && y <= cba && y >= cbb) clist[n1++] = cc;
+      }
+      for (int cm = cb; cm <= ca; ++cm)
+        for (int cbm = (cbb > cm ? cbb : cm); cbm <= cba; ++cbm) {
+          const int t = canon_index(cm * q + cbm, ncap);
+          if (sl.f(BF_G, t) == 0) continue;
+          mlist[n2] = t; mro[n2] = sl.rowoff[t * P + a]; mco[n2] = sl.coloff[t * P + b]; ++n2;
         }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < TILE; ++kk) cfma(part, As[ty][kk], Bs[kk][tx]);
-        __syncthreads();
-      }
-      if (ok) {
-        if (mine) flops += 8ull * (unsigned long long)(k1 - k0) + 8ull;
-        const int dk = ca - cb, db = cba - cbb;
-        const double2 uk = fk[fock_off(dk) + (ca - cm) * (dk + 1) + (ca - xc)];
-        const double2 ub = fk[fock_off(db) + (cba - cbm) * (db + 1) + (cba - yc)];
-        const double2 u = cmul(uk, cconj(ub));
-        cfma(acc, u, to_d2(part));
-      }
+      ncl = n1; nml = n2;
     }
-    const int i = i0 + ty, qq = q0 + tx;
-    if (i < r && qq < c) {
-      double sc = lA[rA[ty]] * lB[cB[tx]];
-      sl.theta[sl.f(BF_TOFF, t) + (long long)i * c + qq] = cscale(acc, sc);
+    __syncthreads();
+    const int nc = ncl, nm = nml;
+    const int na = segA[a + 1] - segA[a], nb = segB[b + 1] - segB[b];
+    const int a0 = segA[a], b0 = segB[b];
+    const int dk = ca - cb, db = cba - cbb;
+    for (int mc0 = 0; mc0 < nm; mc0 += MCH) {
+      const int nq = (nm - mc0) < MCH ? (nm - mc0) : MCH;
+      for (int i0 = 0; i0 < na; i0 += TILE)
+        for (int j0 = 0; j0 < nb; j0 += TILE) {
+          const int i = i0 + ty, jc = j0 + tx;
+          const bool valid = (i < na) && (jc < nb);
+          C acc[MCH];
+#pragma unroll
+          for (int k = 0; k < MCH; ++k) acc[k] = zero_e<C>();
+          for (int ci = 0; ci < nc; ++ci) {
+            const int cc = clist[ci];
+            const int k0 = segC[cc], k1 = segC[cc + 1];
+            const int xc = pair_c(cc, ncap), yc = pair_cb(cc, ncap);
+            C part = zero_e<C>();
+            for (int kb = k0; kb < k1; kb += TILE) {
+              const int kn = (k1 - kb) < TILE ? (k1 - kb) : TILE;
+              As[ty][tx] = (i0 + ty < na && tx < kn) ? cvt<C>(G1[(long long)(a0 + i0 + ty) * D + kb + tx])
+                                                      : zero_e<C>();
+              Bs[ty][tx] = (ty < kn && j0 + tx < nb)
+                               ? cvt<C>(cscale(G2[(long long)(kb + ty) * D + b0 + j0 + tx], lC[kb + ty]))
+                               : zero_e<C>();
+              __syncthreads();
+              if (valid)
+                for (int kk = 0; kk < kn; ++kk) cfma(part, As[ty][kk], Bs[kk][tx]);
+              __syncthreads();
+            }
+            if (valid) {
+              flops += 8ull * (unsigned long long)(k1 - k0) + 8ull * nq;
+              for (int k = 0; k < nq; ++k) {
+                const int m = sl.f(BF_M, mlist[mc0 + k]);
+                const int cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
+                const C uk = fk[fock_off(dk) + (ca - cm) * (dk + 1) + (ca - xc)];
+                const C ub = fk[fock_off(db) + (cba - cbm) * (db + 1) + (cba - yc)];
+                cfma(acc[k], cmul(uk, cj(ub)), part);
+              }
+            }
+          }
+          if (valid) {
+            const R sc = (R)(lA[a0 + i] * lB[b0 + jc]);
+            for (int k = 0; k < nq; ++k) {
+              const int t = mlist[mc0 + k];
+              const int ccols = sl.f(BF_C, t);
+              Th[sl.f(BF_TOFF, t) + (long long)(mro[mc0 + k] + i) * ccols + (mco[mc0 + k] + jc)] =
+                  cscale(acc[k], sc);
+            }
+          }
+        }
     }
   }
   if (st.ctr) {
     flops = __reduce_add_sync(0xffffffffu, (unsigned)flops);
-    if ((threadIdx.x & 31) == 0 && flops) atomicAdd(st.ctr + CTR_THETA, flops);
+    if ((tid & 31) == 0 && flops) atomicAdd(st.ctr + CTR_THETA, flops);
   }
 }
 
 // ---------------------------------------------------------------- k_gram
 // Upper-triangular 16 x 16 tiles of G = Theta Theta^dag (side 0) or Theta^dag Theta.
+template <typename R>
 __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr) {
+  typedef typename Prec<R>::C C;
   const int s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
   const int Pc = ws.Pc;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  __shared__ double2 As[TILE][TILE + 1], Bs[TILE][TILE + 1];
+  __shared__ C As[TILE][TILE + 1], Bs[TILE][TILE + 1];
   __shared__ int gpre[MPO_PC_MAX + 1];
   for (int t = threadIdx.x; t <= Pc; t += blockDim.x) gpre[t] = sl.f(BF_GT, t);
   __syncthreads();
+  const C* ThAll = reinterpret_cast<const C*>(sl.theta);
+  C* GAll = reinterpret_cast<C*>(sl.G);
   const int total = sl.scal[SS_GTILES];
   unsigned long long flops = 0;
   for (int z = blockIdx.x; z < total; z += gridDim.x) {
     const int t = find_block(gpre, Pc + 1, z);
     const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), gg = sl.f(BF_G, t), side = sl.f(BF_SIDE, t);
-    const double2* Th = sl.theta + sl.f(BF_TOFF, t);
-    double2* Gm = sl.G + sl.f(BF_GOFF, t);
+    const C* Th = ThAll + sl.f(BF_TOFF, t);
+    C* Gm = GAll + sl.f(BF_GOFF, t);
     const int nt = (gg + TILE - 1) / TILE;
     int rem = z - gpre[t], ti = 0;
     while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
     const int tj = ti + rem;
     const int K = side == 0 ? c : r;
-    double2 acc = make_double2(0.0, 0.0);
+    C acc = zero_e<C>();
     for (int k0 = 0; k0 < K; k0 += TILE) {
       __syncthreads();
       if (side == 0) {
         int ia = ti * TILE + ty, ib = tj * TILE + ty, kk = k0 + tx;
-        As[ty][tx] = (ia < gg && kk < K) ? Th[(long long)ia * c + kk] : make_double2(0, 0);
-        Bs[ty][tx] = (ib < gg && kk < K) ? Th[(long long)ib * c + kk] : make_double2(0, 0);
+        As[ty][tx] = (ia < gg && kk < K) ? Th[(long long)ia * c + kk] : zero_e<C>();
+        Bs[ty][tx] = (ib < gg && kk < K) ? Th[(long long)ib * c + kk] : zero_e<C>();
       } else {
         int kr = k0 + ty, ja = ti * TILE + tx, jb = tj * TILE + tx;
-        As[ty][tx] = (kr < K && ja < gg) ? Th[(long long)kr * c + ja] : make_double2(0, 0);
-        Bs[ty][tx] = (kr < K && jb < gg) ? Th[(long long)kr * c + jb] : make_double2(0, 0);
+        As[ty][tx] = (kr < K && ja < gg) ? Th[(long long)kr * c + ja] : zero_e<C>();
+        Bs[ty][tx] = (kr < K && jb < gg) ? Th[(long long)kr * c + jb] : zero_e<C>();
       }
       __syncthreads();
+      const int kn = (K - k0) < TILE ? (K - k0) : TILE;
       if (side == 0) {
-#pragma unroll
-        for (int kk = 0; kk < TILE; ++kk) cfma_cj(acc, Bs[tx][kk], As[ty][kk]);
+        for (int kk = 0; kk < kn; ++kk) cfma_cj(acc, Bs[tx][kk], As[ty][kk]);
       } else {
-#pragma unroll
-        for (int kk = 0; kk < TILE; ++kk) cfma_cj(acc, As[kk][ty], Bs[kk][tx]);
+        for (int kk = 0; kk < kn; ++kk) cfma_cj(acc, As[kk][ty], Bs[kk][tx]);
       }
     }
     const int gi = ti * TILE + ty, gj = tj * TILE + tx;
@@ -356,9 +508,11 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
     if (gi < gg && gj < gg) {
       if (ti < tj || ty < tx) {
         Gm[(long long)gi * gg + gj] = acc;
-        Gm[(long long)gj * gg + gi] = cconj(acc);
+        Gm[(long long)gj * gg + gi] = cj(acc);
       } else if (ty == tx) {
-        Gm[(long long)gi * gg + gi] = make_double2(acc.x, 0.0);
+        C d = acc;
+        d.y = 0;
+        Gm[(long long)gi * gg + gi] = d;
       }
     }
   }
@@ -368,17 +522,109 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
   }
 }
 
-// ---------------------------------------------------------------- k_eig
+// ---------------------------------------------------------------- Jacobi core
 // Cyclic Jacobi with the round-robin (circle) pairing: n/2 disjoint rotations per
-// round, n-1 rounds per sweep.  For the pair (p, q) with g = G_pq = |g| e^{i psi}:
-// D = diag(1, e^{-i psi}) makes the 2x2 block real, the real rotation
+// round, n-1 rounds per sweep.  For the pair (p, q) with g = G_pq = |g| e:
+// D = diag(1, conj(e)) makes the 2x2 block real, the real rotation
 // R = [[c, s], [-s, c]] with t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
 // tau = (G_qq - G_pp) / (2|g|) annihilates it, and J = D R is applied as
-// G <- J^dag G J, V <- V J.
-struct RotPair { int p, q; double c, s; double2 e; };
+// G <- J^dag G J, V <- V J.  E = R for real symmetric, E = complex for Hermitian.
+template <typename R, typename E> struct Rot { int p, q; R c, s; E e; };
 
-__device__ __forceinline__ void mirror_coord(const Slot& sl, const MpoDev& st, const GateDesc& g,
-                                             int t, int side, int i, const int* segX, int& mi) {
+template <typename R, typename E>
+__device__ int jacobi(E* A, E* V, int n, Rot<R, E>* rot, int* flags, R tol_rel, R tol_abs_rel) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int np = n + (n & 1), half = np / 2;
+  for (int e = tid; e < n * n; e += nth) V[e] = ((e / n) == (e % n)) ? unit_e<E>() : zero_e<E>();
+  __syncthreads();
+  R dm = 0;
+  for (int i = 0; i < n; ++i) dm = fmax(dm, absv(re(A[(long long)i * n + i])));  // every thread
+  const R tol_abs = tol_abs_rel * dm;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    __syncthreads();  // every thread has read flags[0] of the previous sweep
+    if (tid == 0) flags[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int k = tid; k < half; k += nth) {
+        int p, qq;
+        if (k == 0) { p = rnd; qq = np - 1; }
+        else { p = (rnd + k) % (np - 1); qq = (rnd - k + np - 1) % (np - 1); }
+        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
+        Rot<R, E> rp;
+        rp.p = p; rp.q = -1; rp.c = 1; rp.s = 0; rp.e = unit_e<E>();
+        if (qq < n) {
+          const R a = re(A[(long long)p * n + p]), b = re(A[(long long)qq * n + qq]);
+          const E gpq = A[(long long)p * n + qq];
+          const R hh = absv(gpq);
+          if (hh > tol_rel * sqrt(fabs(a * b)) && hh > tol_abs) {
+            const R tau = (b - a) / (2 * hh);
+            const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+            rp.q = qq;
+            rp.c = (R)1 / sqrt((R)1 + tt * tt);
+            rp.s = tt * rp.c;
+            rp.e = divr<E, R>(gpq, hh);
+            flags[0] = 1;
+            atomicAdd(&flags[1], 1);
+          }
+        }
+        rot[k] = rp;
+      }
+      __syncthreads();
+      // columns: [x, y] <- [c x - s y conj(e), s x + c y conj(e)]
+      for (int w2 = tid; w2 < n * half; w2 += nth) {
+        const int i = w2 / half, k = w2 % half;
+        const Rot<R, E> rp = rot[k];
+        if (rp.q < 0) continue;
+        const E ec = cj(rp.e);
+        E* Ai = A + (long long)i * n;
+        const E x = Ai[rp.p], ys = mulv(Ai[rp.q], ec);
+        Ai[rp.p] = lin(rp.c, x, -rp.s, ys);
+        Ai[rp.q] = lin(rp.s, x, rp.c, ys);
+        E* Vi = V + (long long)i * n;
+        const E vx = Vi[rp.p], vys = mulv(Vi[rp.q], ec);
+        Vi[rp.p] = lin(rp.c, vx, -rp.s, vys);
+        Vi[rp.q] = lin(rp.s, vx, rp.c, vys);
+      }
+      __syncthreads();
+      // rows: [x; y] <- [c x - s e y; s x + c e y]
+      for (int w2 = tid; w2 < n * half; w2 += nth) {
+        const int k = w2 / n, i = w2 % n;
+        const Rot<R, E> rp = rot[k];
+        if (rp.q < 0) continue;
+        const E x = A[(long long)rp.p * n + i], ye = mulv(rp.e, A[(long long)rp.q * n + i]);
+        A[(long long)rp.p * n + i] = lin(rp.c, x, -rp.s, ye);
+        A[(long long)rp.q * n + i] = lin(rp.s, x, rp.c, ye);
+      }
+      __syncthreads();
+    }
+    if (!flags[0]) break;
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// Shared-memory layout of the eigensolver for blocks up to nmax: rotation list,
+// mirror positions, bond segments, flags, then A and V.
+struct EigLayout {
+  size_t rot, mpos, seg, flags, A, total_fixed;
+};
+template <typename R>
+__host__ __device__ inline EigLayout eig_layout(int nmax) {
+  typedef typename Prec<R>::C C;
+  EigLayout L;
+  size_t o = 0;
+  L.rot = o; o += (size_t)(nmax / 2 + 1) * sizeof(Rot<R, C>); o = (o + 15) & ~(size_t)15;
+  L.mpos = o; o += (size_t)nmax * sizeof(int); o = (o + 15) & ~(size_t)15;
+  L.seg = o; o += (size_t)(MPO_P_MAX + 2) * sizeof(int); o = (o + 15) & ~(size_t)15;
+  L.flags = o; o += 4 * sizeof(int); o = (o + 15) & ~(size_t)15;
+  L.A = o;
+  L.total_fixed = o;
+  return L;
+}
+
+__device__ __forceinline__ int mirror_coord(const Slot& sl, const MpoDev& st, const GateDesc& g, int t,
+                                            int side, int i, const int* segX) {
   const int ncap = st.ncap, P = st.P, D = st.D, M = st.M;
   const long long bX = (long long)g.inst * (M + 1) + g.j + (side == 0 ? 0 : 2);
   const int idx = side == 0 ? sl.rowmap[sl.f(BF_RMOFF, t) + i] : sl.colmap[sl.f(BF_CMOFF, t) + i];
@@ -388,187 +634,131 @@ __device__ __forceinline__ void mirror_coord(const Slot& sl, const MpoDev& st, c
   const int pos = idx - segX[pa];
   if (off < 0 || pos >= segX[pm + 1] - segX[pm]) {  // mirror structure broken: never index with it
     dev_set_error(st.err, DEV_ERR_INTERNAL, 8000 + t);
-    mi = i;
-    return;
+    return i;
   }
-  mi = off + pos;
+  return off + pos;
 }
 
-__global__ void __launch_bounds__(256) k_eig(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
-                                             int smem_bytes) {
+// ---------------------------------------------------------------- k_eig
+// One CTA per canonical block of size class SMALL (n <= SMALL_N) or large (n > SMALL_N).
+template <typename R, bool SMALL>
+__global__ void __launch_bounds__(SMALL ? 128 : 256) k_eig(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
+                                                          int nmax, int smem_bytes) {
+  typedef typename Prec<R>::C C;
   const int t = blockIdx.x, s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS] || t >= ws.Pc) return;
   const int n = sl.f(BF_G, t);
-  if (n == 0) return;
+  if (n == 0 || (SMALL ? n > SMALL_N : n <= SMALL_N)) return;
   const GateDesc g = gates[s];
   const int side = sl.f(BF_SIDE, t), m = sl.f(BF_M, t);
   const int ncap = st.ncap, P = st.P, M = st.M;
   const bool selfm = pair_mirror(m, ncap) == m;
-  const int np = n + (n & 1), half = np / 2;
   const int tid = threadIdx.x, nth = blockDim.x;
   extern __shared__ __align__(16) unsigned char smem[];
-  RotPair* rot = reinterpret_cast<RotPair*>(smem);
-  int* mpos = reinterpret_cast<int*>(rot + (ws.D / 2 + 1));
-  int* segX = mpos + ws.D;
-  double* red = reinterpret_cast<double*>(segX + MPO_P_MAX + 2);
-  int* flags = reinterpret_cast<int*>(red + 2);
-  size_t fixed = (size_t)(ws.D / 2 + 1) * sizeof(RotPair) + ws.D * sizeof(int) +
-                 (MPO_P_MAX + 2) * sizeof(int) + 2 * sizeof(double) + 4 * sizeof(int);
-  fixed = (fixed + 15) & ~(size_t)15;
-  const bool in_smem = fixed + 2ull * n * n * sizeof(double2) <= (size_t)smem_bytes;
-  double2* gG = sl.G + sl.f(BF_GOFF, t);
-  double2* gV = sl.V + sl.f(BF_GOFF, t);
-  double2* A = in_smem ? reinterpret_cast<double2*>(smem + fixed) : gG;
-  double2* V = in_smem ? A + (long long)n * n : gV;
-
+  const EigLayout L = eig_layout<R>(nmax);
+  int* mpos = reinterpret_cast<int*>(smem + L.mpos);
+  int* segX = reinterpret_cast<int*>(smem + L.seg);
+  int* flags = reinterpret_cast<int*>(smem + L.flags);
+  C* gG = reinterpret_cast<C*>(sl.G) + sl.f(BF_GOFF, t);
+  C* gV = reinterpret_cast<C*>(sl.V) + sl.f(BF_GOFF, t);
+  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
+  int sweeps;
   if (selfm) {
+    const bool in_smem = L.total_fixed + 2ull * n * n * sizeof(R) <= (size_t)smem_bytes;
     const long long bX = (long long)g.inst * (M + 1) + g.j + (side == 0 ? 0 : 2);
     for (int p = tid; p <= P; p += nth) segX[p] = st.segoff[bX * (P + 1) + p];
     __syncthreads();
-    for (int i = tid; i < n; i += nth) { int mi; mirror_coord(sl, st, g, t, side, i, segX, mi); mpos[i] = mi; }
+    for (int i = tid; i < n; i += nth) mpos[i] = mirror_coord(sl, st, g, t, side, i, segX);
     __syncthreads();
-    // realified Gram in the basis e_i (fixed), (e_p + e_q)/sqrt2 at p, i(e_p - e_q)/sqrt2 at q (p < q)
-    double2* dst = in_smem ? A : gV;  // global mode: stage in V, copy back below
-    const double h = 0.70710678118654752440;
+    // real Gram in the basis e_i (fixed), (e_p + e_q)/sqrt2 at p, i(e_p - e_q)/sqrt2 at q (p < q)
+    R* A = in_smem ? reinterpret_cast<R*>(smem + L.A) : reinterpret_cast<R*>(gV);
+    R* V = in_smem ? A + (long long)n * n : reinterpret_cast<R*>(gG);
+    const R h = (R)0.70710678118654752440;
     for (int e = tid; e < n * n; e += nth) {
       const int i = e / n, j = e % n;
-      int ai[2], bj[2]; double2 wa[2], wb[2]; int na = 0, nb = 0;
+      int ai[2], bj[2]; C wa[2], wb[2]; int na = 0, nb = 0;
       const int pi = mpos[i], pj = mpos[j];
-      if (pi == i) { ai[0] = i; wa[0] = make_double2(1, 0); na = 1; }
-      else if (i < pi) { ai[0] = i; wa[0] = make_double2(h, 0); ai[1] = pi; wa[1] = make_double2(h, 0); na = 2; }
-      else { ai[0] = pi; wa[0] = make_double2(0, h); ai[1] = i; wa[1] = make_double2(0, -h); na = 2; }
-      if (pj == j) { bj[0] = j; wb[0] = make_double2(1, 0); nb = 1; }
-      else if (j < pj) { bj[0] = j; wb[0] = make_double2(h, 0); bj[1] = pj; wb[1] = make_double2(h, 0); nb = 2; }
-      else { bj[0] = pj; wb[0] = make_double2(0, h); bj[1] = j; wb[1] = make_double2(0, -h); nb = 2; }
-      double acc = 0.0;
+      if (pi == i) { ai[0] = i; wa[0] = mk((R)1, (R)0); na = 1; }
+      else if (i < pi) { ai[0] = i; wa[0] = mk(h, (R)0); ai[1] = pi; wa[1] = mk(h, (R)0); na = 2; }
+      else { ai[0] = pi; wa[0] = mk((R)0, h); ai[1] = i; wa[1] = mk((R)0, -h); na = 2; }
+      if (pj == j) { bj[0] = j; wb[0] = mk((R)1, (R)0); nb = 1; }
+      else if (j < pj) { bj[0] = j; wb[0] = mk(h, (R)0); bj[1] = pj; wb[1] = mk(h, (R)0); nb = 2; }
+      else { bj[0] = pj; wb[0] = mk((R)0, h); bj[1] = j; wb[1] = mk((R)0, -h); nb = 2; }
+      R acc = 0;
       for (int x = 0; x < na; ++x)
-        for (int y = 0; y < nb; ++y) {
-          double2 v = cmul(cmul(cconj(wa[x]), gG[(long long)ai[x] * n + bj[y]]), wb[y]);
-          acc += v.x;
-        }
-      dst[(long long)i * n + j] = make_double2(acc, 0.0);
+        for (int y = 0; y < nb; ++y) acc += cmul(cmul(cj(wa[x]), gG[(long long)ai[x] * n + bj[y]]), wb[y]).x;
+      A[(long long)i * n + j] = acc;
+    }
+    __syncthreads();  // gG fully read before V (global mode) overwrites it
+    sweeps = jacobi<R, R>(A, V, n, reinterpret_cast<Rot<R, R>*>(smem + L.rot), flags, Prec<R>::tol_rel,
+                          Prec<R>::tol_abs);
+    // eigenvalues first (A's storage is reused below in global mode)
+    const int coff = sl.f(BF_COFF, t);
+    for (int i = tid; i < n; i += nth) {
+      const R wi = A[(long long)i * n + i];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) {
+        const R wj = A[(long long)j * n + j];
+        rank += (wj > wi) || (wj == wi && j < i);
+      }
+      if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4000 + t);
+      sl.sval[coff + rank] = sqrt(fmax((double)wi, 0.0));
+      sl.perm[coff + rank] = i;
     }
     __syncthreads();
-    if (!in_smem) {
-      for (int e = tid; e < n * n; e += nth) A[e] = gV[e];
-      __syncthreads();
-    }
-  } else if (in_smem) {
-    for (int e = tid; e < n * n; e += nth) A[e] = gG[e];
-  }
-  for (int e = tid; e < n * n; e += nth) V[e] = make_double2((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
-  if (tid == 0) {
-    double dm = 0.0;
-    for (int i = 0; i < n; ++i) dm = fmax(dm, fabs(A[(long long)i * n + i].x));
-    red[0] = dm;
-  }
-  __syncthreads();
-  const double tol_rel = 1e-15, tol_abs = 1e-18 * red[0];
-  if (tid == 0) flags[1] = 0;
-  int sweep = 0;
-  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
-    if (tid == 0) flags[0] = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int k = tid; k < half; k += nth) {
-        int p, qq;
-        if (k == 0) { p = rnd; qq = np - 1; }
-        else { p = (rnd + k) % (np - 1); qq = (rnd - k + np - 1) % (np - 1); }
-        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
-        RotPair rp; rp.p = p; rp.q = qq; rp.c = 1.0; rp.s = 0.0; rp.e = make_double2(1.0, 0.0);
-        if (qq < n) {
-          const double a = A[(long long)p * n + p].x, b = A[(long long)qq * n + qq].x;
-          const double2 gpq = A[(long long)p * n + qq];
-          const double hh = hypot(gpq.x, gpq.y);
-          if (hh > tol_rel * sqrt(fabs(a * b)) && hh > tol_abs) {
-            const double tau = (b - a) / (2.0 * hh);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            rp.c = 1.0 / sqrt(1.0 + tt * tt);
-            rp.s = tt * rp.c;
-            rp.e = make_double2(gpq.x / hh, gpq.y / hh);
-            flags[0] = 1;
-            if (st.ctr) atomicAdd(&flags[1], 1);
-          } else rp.q = -1;
-        } else rp.q = -1;
-        rot[k] = rp;
-      }
-      __syncthreads();
-      // columns: [x, y] <- [x, y] [[c, s], [-s conj(e), c conj(e)]]
-      for (int w2 = tid; w2 < n * half; w2 += nth) {
-        const int i = w2 / half, k = w2 % half;
-        const RotPair rp = rot[k];
-        if (rp.q < 0) continue;
-        const double2 ec = cconj(rp.e);
-        double2* Ai = A + (long long)i * n;
-        const double2 x = Ai[rp.p], y = Ai[rp.q];
-        const double2 ys = cmul(y, ec);
-        Ai[rp.p] = make_double2(rp.c * x.x - rp.s * ys.x, rp.c * x.y - rp.s * ys.y);
-        Ai[rp.q] = make_double2(rp.s * x.x + rp.c * ys.x, rp.s * x.y + rp.c * ys.y);
-        double2* Vi = V + (long long)i * n;
-        const double2 vx = Vi[rp.p], vy = Vi[rp.q];
-        const double2 vys = cmul(vy, ec);
-        Vi[rp.p] = make_double2(rp.c * vx.x - rp.s * vys.x, rp.c * vx.y - rp.s * vys.y);
-        Vi[rp.q] = make_double2(rp.s * vx.x + rp.c * vys.x, rp.s * vx.y + rp.c * vys.y);
-      }
-      __syncthreads();
-      // rows: [x; y] <- J^dag [x; y] = [[c, -s e], [s, c e]] [x; y]
-      for (int w2 = tid; w2 < n * half; w2 += nth) {
-        const int k = w2 / n, i = w2 % n;
-        const RotPair rp = rot[k];
-        if (rp.q < 0) continue;
-        const double2 x = A[(long long)rp.p * n + i], y = A[(long long)rp.q * n + i];
-        const double2 ye = cmul(y, rp.e);
-        A[(long long)rp.p * n + i] = make_double2(rp.c * x.x - rp.s * ye.x, rp.c * x.y - rp.s * ye.y);
-        A[(long long)rp.q * n + i] = make_double2(rp.s * x.x + rp.c * ye.x, rp.s * x.y + rp.c * ye.y);
-      }
-      __syncthreads();
-    }
-    const int any = flags[0];
-    __syncthreads();
-    if (!any) break;
-  }
-  if (sweep >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3000 + t);
-  if (st.ctr && tid == 0) {
-    // per active rotation and per index: A columns, A rows and V columns, 18 flops each
-    atomicAdd(st.ctr + CTR_EIG, 54ull * (unsigned long long)n * (unsigned long long)flags[1]);
-    atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweep + 1));
-    atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
-  }
-  // eigenvalues, descending ranks (ties by index)
-  const int coff = sl.f(BF_COFF, t);
-  for (int i = tid; i < n; i += nth) {
-    const double wi = A[(long long)i * n + i].x;
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double wj = A[(long long)j * n + j].x;
-      rank += (wj > wi) || (wj == wi && j < i);
-    }
-    if (!isfinite(wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4000 + t);
-    sl.sval[coff + rank] = sqrt(fmax(wi, 0.0));
-    sl.perm[coff + rank] = i;
-  }
-  __syncthreads();  // every diagonal read above happens before A is reused below
-  // eigenvectors out to gV (back to the original basis for self-mirror blocks)
-  if (selfm) {
-    const double h = 0.70710678118654752440;
+    // eigenvectors back to the original basis: x = W x~ (x~ real).  In global mode A
+    // (dead now) shares gV's storage and V lives in gG, so writing gV is safe.
     for (int e = tid; e < n * n; e += nth) {
       const int i = e / n, k = e % n;
       const int pi = mpos[i];
-      double2 out;
-      if (pi == i) out = make_double2(V[(long long)i * n + k].x, 0.0);
-      else if (i < pi) out = make_double2(h * V[(long long)i * n + k].x, h * V[(long long)pi * n + k].x);
-      else out = make_double2(h * V[(long long)pi * n + k].x, -h * V[(long long)i * n + k].x);
-      if (in_smem) gV[e] = out;
-      else A[e] = out;  // V lives in gV: stage through A (no longer needed)
+      C out;
+      if (pi == i) out = mk(V[(long long)i * n + k], (R)0);
+      else if (i < pi) out = mk(h * V[(long long)i * n + k], h * V[(long long)pi * n + k]);
+      else out = mk(h * V[(long long)pi * n + k], -h * V[(long long)i * n + k]);
+      gV[e] = out;
     }
-    if (!in_smem) {
-      __syncthreads();
-      for (int e = tid; e < n * n; e += nth) gV[e] = A[e];
+    if (st.ctr && tid == 0) {
+      // real rotation: 6 flops per index for A columns, A rows and V columns each
+      atomicAdd(st.ctr + CTR_EIG, 18ull * (unsigned long long)n * (unsigned long long)flags[1]);
+      atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
+      atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
     }
-  } else if (in_smem) {
+    if (sweeps >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3000 + t);
+    return;
+  }
+  // complex Hermitian block
+  const bool in_smem = L.total_fixed + 2ull * n * n * sizeof(C) <= (size_t)smem_bytes;
+  C* A = in_smem ? reinterpret_cast<C*>(smem + L.A) : gG;
+  C* V = in_smem ? A + (long long)n * n : gV;
+  if (in_smem) {
+    for (int e = tid; e < n * n; e += nth) A[e] = gG[e];
+  }
+  __syncthreads();
+  sweeps = jacobi<R, C>(A, V, n, reinterpret_cast<Rot<R, C>*>(smem + L.rot), flags, Prec<R>::tol_rel,
+                        Prec<R>::tol_abs);
+  const int coff = sl.f(BF_COFF, t);
+  for (int i = tid; i < n; i += nth) {
+    const R wi = A[(long long)i * n + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const R wj = A[(long long)j * n + j].x;
+      rank += (wj > wi) || (wj == wi && j < i);
+    }
+    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4000 + t);
+    sl.sval[coff + rank] = sqrt(fmax((double)wi, 0.0));
+    sl.perm[coff + rank] = i;
+  }
+  if (in_smem) {
     for (int e = tid; e < n * n; e += nth) gV[e] = V[e];
   }
+  if (st.ctr && tid == 0) {
+    // per active rotation and per index: A columns, A rows and V columns, 18 flops each
+    atomicAdd(st.ctr + CTR_EIG, 54ull * (unsigned long long)n * (unsigned long long)flags[1]);
+    atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
+    atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+  }
+  if (sweeps >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3000 + t);
 }
 
 // ---------------------------------------------------------------- k_select
@@ -589,14 +779,12 @@ __device__ double block_sum(double v, double* red) {
 // (s desc, m asc, k asc); the list has pair index ml and alive length len.
 __device__ __forceinline__ int count_before(const double* lst, int len, int ml, double sv, int m, int k) {
   if (ml == m) return k;
-  // first index with lst[i] < sv (strictly smaller), and first with lst[i] <= sv
   int lo = 0, hi = len;
   while (lo < hi) { int mid = (lo + hi) >> 1; if (lst[mid] > sv) lo = mid + 1; else hi = mid; }
-  int gt = lo;
-  if (ml > m) return gt;
+  if (ml > m) return lo;
   hi = len;
   while (lo < hi) { int mid = (lo + hi) >> 1; if (lst[mid] >= sv) lo = mid + 1; else hi = mid; }
-  return lo;  // includes equal values
+  return lo;
 }
 
 __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
@@ -608,7 +796,7 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
   const int ncap = st.ncap, P = st.P, M = st.M, D = st.D, Pc = ws.Pc;
   const int tid = threadIdx.x, nth = blockDim.x;
   __shared__ double red[1024];
-  __shared__ int lstart[2 * MPO_PC_MAX + 1];   // prefix of alive counts over lists
+  __shared__ int lstart[2 * MPO_PC_MAX + 1];
   __shared__ int lalive[2 * MPO_PC_MAX], lkept[2 * MPO_PC_MAX], lpair[2 * MPO_PC_MAX];
   __shared__ int newseg[MPO_P_MAX + 1];
   __shared__ int keep_sh, nalive_sh;
@@ -675,8 +863,7 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
     for (int e = tid; e < nalive; e += nth) {
       const int l = find_block(lstart, NL + 1, e);
       const int k = e - lstart[l];
-      const int t = l >> 1;
-      const double sv = sl.sval[sl.f(BF_COFF, t) + k];
+      const double sv = sl.sval[sl.f(BF_COFF, l >> 1) + k];
       const int mpair = lpair[l];
       int rank = 0;
       for (int l2 = 0; l2 < NL; ++l2) {
@@ -744,22 +931,176 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
     }
   }
   for (int p = tid; p <= P; p += nth) st.segoff[bC * (P + 1) + p] = newseg[p];
-  keptw = block_sum(keptw, red);
+  keptw = block_sum(keptw, red);  // its barriers also publish the lC writes above
   const int chinew = newseg[P];
   double ent = 0.0;
   for (int i = tid; i < chinew; i += nth) {
     const double pr = lC[i] * lC[i] / keptw;
     if (pr > 0.0) ent -= pr * log2(pr);
   }
-  __syncthreads();  // lC writes above are visible to every thread
   ent = block_sum(ent, red);
   if (tid == 0) {
     st.chi[bC] = chinew;
     st.entropy[bC] = ent;
-    const double eps = tot > 0.0 ? (tot - keptw) / tot : 0.0;
+    const double eps = tot > 0.0 ? fmax(0.0, (tot - keptw) / tot) : 0.0;  // rounding can go below 0
     sl.dscal[0] = eps;
     if (disc != nullptr && g.out >= 0) disc[g.out] = eps;
     if (chinew == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 7000);
+  }
+}
+
+
+// ---------------------------------------------------------------- k_refine
+// One-sided Jacobi (Hestenes) refinement of each canonical block's SVD.  The Gram
+// eigenvectors V (n x n, from k_eig) give W = Theta V (side 1, n = cols) or
+// W = Theta^dag V (side 0, n = rows), whose n columns are orthogonal up to the Gram
+// eigensolver's error.  Sweeps of pairwise rotations that orthogonalise the columns
+// of W (the 2x2 Gram [[|w_p|^2, w_p^dag w_q], [., |w_q|^2]] recomputed from W at each
+// step, the same rotation applied to V) converge quadratically to the SVD of Theta
+// without squaring its condition number: s_k = |w_k|.  Both factors come out:
+// side 1: X[:, k] = w_k / s_k, Y[k, :] = conj(v_k);  side 0: X[:, k] = v_k,
+// Y[k, :] = conj(w_k) / s_k.  W (h x n) and V (n x n) are column-major, in shared
+// memory when they fit, else in the slot scratch (W buffer, G buffer).
+template <typename R>
+__global__ void __launch_bounds__(256) k_refine(MpoDev st, SlotWS ws, int smem_bytes) {
+  typedef typename Prec<R>::C C;
+  const int t = blockIdx.x, s = blockIdx.y;
+  Slot sl = get_slot(ws, s);
+  if (sl.scal[SS_STATUS] || t >= ws.Pc) return;
+  const int n = sl.f(BF_G, t);
+  if (n == 0) return;
+  const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
+  const int h = side == 0 ? c : r;
+  const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* flags = reinterpret_cast<int*>(smem);
+  R* nrm = reinterpret_cast<R*>(smem + 16);  // [max(n, 32)]: column norms, also per-warp scratch
+  const int nn = n > 32 ? n : 32;
+  size_t off = 16 + (((size_t)nn * sizeof(R) + 15) & ~(size_t)15);
+  const bool in_smem = off + ((size_t)h * n + (size_t)n * n) * sizeof(C) <= (size_t)smem_bytes;
+  const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
+  const C* V0 = reinterpret_cast<const C*>(sl.V) + sl.f(BF_GOFF, t);   // row-major from k_eig
+  C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);
+  C* gVc = reinterpret_cast<C*>(sl.G) + sl.f(BF_GOFF, t);             // the Gram is dead now
+  C* W = in_smem ? reinterpret_cast<C*>(smem + off) : gW;
+  C* Vc = in_smem ? W + (size_t)h * n : gVc;
+  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
+  for (int e = tid; e < n * n; e += nth) {  // column-major copy of V
+    const int k = e / n, i = e % n;
+    Vc[e] = V0[(long long)i * n + k];
+  }
+  __syncthreads();
+  for (int e = tid; e < h * n; e += nth) {
+    const int k = e / h, x = e % h;
+    C acc = zero_e<C>();
+    if (side == 1) {
+      for (int q = 0; q < n; ++q) cfma(acc, Th[(long long)x * c + q], Vc[(long long)k * n + q]);
+    } else {
+      for (int i = 0; i < n; ++i) cfma_cj(acc, Th[(long long)i * c + x], Vc[(long long)k * n + i]);
+    }
+    W[e] = acc;
+  }
+  __syncthreads();
+  // largest column norm^2 (scale of the absolute threshold)
+  R mx = 0;
+  for (int k = warp; k < n; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    mx = fmax(mx, a);
+  }
+  if (lane == 0) nrm[warp] = mx;
+  __syncthreads();
+  mx = 0;
+  for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
+  __syncthreads();
+  const R tol_abs = Prec<R>::os_abs * mx;
+  const int np = n + (n & 1), half = np / 2;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) flags[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int k = warp; k < half; k += nwarp) {
+        int p, qq;
+        if (k == 0) { p = rnd; qq = np - 1; }
+        else { p = (rnd + k) % (np - 1); qq = (rnd - k + np - 1) % (np - 1); }
+        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
+        if (qq >= n) continue;
+        C* wp = W + (long long)p * h;
+        C* wq = W + (long long)qq * h;
+        R al = 0, be = 0;
+        C ga = zero_e<C>();
+        for (int x = lane; x < h; x += 32) {
+          const C a = wp[x], b = wq[x];
+          al += a.x * a.x + a.y * a.y;
+          be += b.x * b.x + b.y * b.y;
+          cfma_cj(ga, a, b);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+        }
+        // self-mirror block: the columns are mirror-symmetric, so w_p^dag w_q is real
+        // in exact arithmetic; its imaginary part is rounding noise and a rotation with
+        // that phase would break the symmetry, so the rotation is kept real
+        if (selfm) ga.y = 0;
+        const R hh = absv(ga);
+        if (!(hh > Prec<R>::os_rel * sqrt(al * be) && hh > tol_abs)) continue;  // warp-uniform
+        const R tau = (be - al) / (2 * hh);
+        const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+        const R cs = (R)1 / sqrt((R)1 + tt * tt), sn = tt * cs;
+        const C ec = cj(divr<C, R>(ga, hh));
+        for (int x = lane; x < h; x += 32) {
+          const C a = wp[x], bs = mulv(wq[x], ec);
+          wp[x] = lin(cs, a, -sn, bs);
+          wq[x] = lin(sn, a, cs, bs);
+        }
+        C* vp = Vc + (long long)p * n;
+        C* vq = Vc + (long long)qq * n;
+        for (int x = lane; x < n; x += 32) {
+          const C a = vp[x], bs = mulv(vq[x], ec);
+          vp[x] = lin(cs, a, -sn, bs);
+          vq[x] = lin(sn, a, cs, bs);
+        }
+        if (lane == 0) { flags[0] = 1; atomicAdd(&flags[1], 1); }
+      }
+      __syncthreads();
+    }
+    const int any = flags[0];
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
+  // singular values = column norms, ranked descending (ties by index)
+  for (int k = warp; k < n; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) nrm[k] = a;
+  }
+  __syncthreads();
+  const int coff = sl.f(BF_COFF, t);
+  for (int i = tid; i < n; i += nth) {
+    const R wi = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4500 + t);
+    sl.sval[coff + rank] = sqrt((double)wi);
+    sl.perm[coff + rank] = i;
+  }
+  if (in_smem) {
+    for (int e = tid; e < h * n; e += nth) gW[e] = W[e];
+    for (int e = tid; e < n * n; e += nth) gVc[e] = Vc[e];
+  }
+  if (st.ctr && tid == 0) {
+    // per applied rotation: 3 inner products (24 h) and 2 x 12 (h + n) for the updates
+    atomicAdd(st.ctr + CTR_REFINE, (unsigned long long)flags[1] * (48ull * h + 24ull * n) +
+                                       8ull * (unsigned long long)h * n * n);
+    atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sweep + 1));
   }
 }
 
@@ -773,11 +1114,12 @@ __device__ __forceinline__ int mirror_index(const int* seg, const int* ch, int a
 }
 
 // ---------------------------------------------------------------- k_resplit
-// For every kept singular triple of a canonical block: X column and Y row (one of
-// them is an eigenvector, the other Theta times it over sigma), written as
+// For every kept singular triple of a canonical block (refined by k_refine):
 // Gamma_j[:, beta] = X / lambda_A and Gamma_{j+1}[beta, :] = Y / lambda_B, plus the
 // conjugated, mirror-permuted copies for the mirror block.
+template <typename R>
 __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+  typedef typename Prec<R>::C C;
   const int s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
@@ -786,8 +1128,6 @@ __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const Gat
   const int tid = threadIdx.x, nth = blockDim.x;
   __shared__ int kpre[MPO_PC_MAX + 1];
   __shared__ int segA[MPO_P_MAX + 1], segB[MPO_P_MAX + 1];
-  extern __shared__ __align__(16) unsigned char smem[];
-  double2* vec = reinterpret_cast<double2*>(smem);  // [D]
   const long long bA = (long long)g.inst * (M + 1) + g.j, bB = bA + 2;
   for (int t = tid; t <= Pc; t += nth) kpre[t] = sl.f(BF_KOFF, t);
   for (int p = tid; p <= P; p += nth) {
@@ -802,70 +1142,39 @@ __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const Gat
   double2* G1 = st.gam + ((long long)g.inst * M + g.j) * D * D;
   double2* G2 = G1 + (long long)D * D;
   const int items = sl.scal[SS_NITEMS];
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   for (int z = blockIdx.x; z < items; z += gridDim.x) {
     const int t = find_block(kpre, Pc + 1, z);
     const int k = z - kpre[t];
     const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), n = sl.f(BF_G, t), side = sl.f(BF_SIDE, t);
+    const int h = side == 0 ? c : r;
     const int mt = sl.f(BF_M, t);
     const bool mir = pair_mirror(mt, ncap) != mt;
     const int coff = sl.f(BF_COFF, t);
-    const double sig = sl.sval[coff + k];
+    const double isig = 1.0 / sl.sval[coff + k];
     const int vc = sl.perm[coff + k];
-    const double2* Vm = sl.V + sl.f(BF_GOFF, t);
-    const double2* Th = sl.theta + sl.f(BF_TOFF, t);
+    const C* wk = reinterpret_cast<const C*>(sl.W) + sl.f(BF_TOFF, t) + (long long)vc * h;
+    const C* vk = reinterpret_cast<const C*>(sl.G) + sl.f(BF_GOFF, t) + (long long)vc * n;
     const int* rmap = sl.rowmap + sl.f(BF_RMOFF, t);
     const int* cmap = sl.colmap + sl.f(BF_CMOFF, t);
     const int beta = sl.f(BF_NEWPOS, t) + k, betam = sl.f(BF_NEWPOS_MIR, t) + k;
-    if (st.ctr && tid == 0) atomicAdd(st.ctr + CTR_RESPLIT, 8ull * (unsigned long long)r * c);
-    __syncthreads();
-    for (int i = tid; i < n; i += nth) vec[i] = Vm[(long long)i * n + vc];
-    __syncthreads();
-    if (side == 0) {
-      // X = eigenvector (rows); Y = X^dag Theta / sigma
-      for (int i = tid; i < r; i += nth) {
-        const int a = rmap[i];
-        G1[(long long)a * D + beta] = cscale(vec[i], 1.0 / lA[a]);
-        if (mir) {
-          const int am = mirror_index(segA, chA, a, ncap, st.err);
-          if (am >= 0) G1[(long long)am * D + betam] = cscale(cconj(vec[i]), 1.0 / lA[am]);
-        }
+    if (st.ctr && tid == 0) atomicAdd(st.ctr + CTR_RESPLIT, 2ull * (unsigned long long)(r + c));
+    // X column (length r) and Y row (length c)
+    for (int i = tid; i < r; i += nth) {
+      const double2 x = side == 1 ? cscale(to_d2(wk[i]), isig) : to_d2(vk[i]);
+      const int a = rmap[i];
+      G1[(long long)a * D + beta] = cscale(x, 1.0 / lA[a]);
+      if (mir) {
+        const int am = mirror_index(segA, chA, a, ncap, st.err);
+        if (am >= 0) G1[(long long)am * D + betam] = cscale(cconj(x), 1.0 / lA[am]);
       }
-      for (int qq = tid; qq < c; qq += nth) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int i = 0; i < r; ++i) cfma_cj(acc, vec[i], Th[(long long)i * c + qq]);
-        const int b = cmap[qq];
-        G2[(long long)beta * D + b] = cscale(acc, 1.0 / (sig * lB[b]));
-        if (mir) {
-          const int bm = mirror_index(segB, chB, b, ncap, st.err);
-          if (bm >= 0) G2[(long long)betam * D + bm] = cscale(cconj(acc), 1.0 / (sig * lB[bm]));
-        }
-      }
-    } else {
-      // Y = eigenvector^dag (cols); X = Theta v / sigma
-      for (int qq = tid; qq < c; qq += nth) {
-        const int b = cmap[qq];
-        G2[(long long)beta * D + b] = cscale(cconj(vec[qq]), 1.0 / lB[b]);
-        if (mir) {
-          const int bm = mirror_index(segB, chB, b, ncap, st.err);
-          if (bm >= 0) G2[(long long)betam * D + bm] = cscale(vec[qq], 1.0 / lB[bm]);
-        }
-      }
-      for (int i = warp; i < r; i += nwarp) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int qq = lane; qq < c; qq += 32) cfma(acc, Th[(long long)i * c + qq], vec[qq]);
-        for (int o = 16; o > 0; o >>= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
-        if (lane == 0) {
-          const int a = rmap[i];
-          G1[(long long)a * D + beta] = cscale(acc, 1.0 / (sig * lA[a]));
-          if (mir) {
-            const int am = mirror_index(segA, chA, a, ncap, st.err);
-            if (am >= 0) G1[(long long)am * D + betam] = cscale(cconj(acc), 1.0 / (sig * lA[am]));
-          }
-        }
+    }
+    for (int qq = tid; qq < c; qq += nth) {
+      const double2 y = side == 1 ? cconj(to_d2(vk[qq])) : cscale(cconj(to_d2(wk[qq])), isig);
+      const int b = cmap[qq];
+      G2[(long long)beta * D + b] = cscale(y, 1.0 / lB[b]);
+      if (mir) {
+        const int bm = mirror_index(segB, chB, b, ncap, st.err);
+        if (bm >= 0) G2[(long long)betam * D + bm] = cscale(cconj(y), 1.0 / lB[bm]);
       }
     }
   }
@@ -903,47 +1212,79 @@ int sm_count() {
   return g_sm_count;
 }
 
-}  // namespace
+constexpr size_t LARGE_SMEM_CAP = 200 * 1024;
+constexpr size_t REFINE_SMEM = 200 * 1024;
 
-size_t eig_smem_bytes(int D) {
-  size_t fixed = (size_t)(D / 2 + 1) * sizeof(RotPair) + D * sizeof(int) + (MPO_P_MAX + 2) * sizeof(int) +
-                 2 * sizeof(double) + 4 * sizeof(int);
-  fixed = (fixed + 15) & ~(size_t)15;
-  size_t full = fixed + 2ull * D * D * sizeof(double2);
-  const size_t cap = 200 * 1024;
-  return full < cap ? full : cap;
+template <typename R>
+size_t eig_smem_large(int D) {
+  typedef typename Prec<R>::C C;
+  const EigLayout L = eig_layout<R>(D);
+  const size_t full = L.total_fixed + 2ull * D * D * sizeof(C);
+  return full < LARGE_SMEM_CAP ? full : LARGE_SMEM_CAP;
+}
+template <typename R>
+size_t eig_smem_small() {
+  typedef typename Prec<R>::C C;
+  const EigLayout L = eig_layout<R>(SMALL_N);
+  return L.total_fixed + 2ull * SMALL_N * SMALL_N * sizeof(C);
 }
 
-// One-time per-process setup (called outside any stream capture).
-cudaError_t gate_module_init() {
-  sm_count();
-  return cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
-// stage_events (optional, 7 events): recorded before each of the 6 stage launches
-// and after the last one, for per-stage timing.
-void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates,
-                  double* d_disc, int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
-  (void)prec;
-  const size_t esm = eig_smem_bytes(ws.D);
+template <typename R>
+void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
+                    cudaStream_t st, cudaEvent_t* ev) {
   const int sms = sm_count();
   int per = (4 * sms + ngates - 1) / ngates;
   if (per < 1) per = 1;
   if (per > 4096) per = 4096;
+  const size_t sm_small = eig_smem_small<R>();
+  const size_t sm_large = eig_smem_large<R>(ws.D);
   if (ev) cudaEventRecord(ev[0], st);
   k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates);
   if (ev) cudaEventRecord(ev[1], st);
-  k_theta<double2><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
+  k_theta<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
   if (ev) cudaEventRecord(ev[2], st);
-  k_gram<<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
+  k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
   if (ev) cudaEventRecord(ev[3], st);
-  k_eig<<<dim3(ws.Pc, ngates), 256, esm, st>>>(s, ws, d_gates, (int)esm);
+  k_eig<R, true><<<dim3(ws.Pc, ngates), 128, sm_small, st>>>(s, ws, d_gates, SMALL_N, (int)sm_small);
+  if (ws.D > SMALL_N)
+    k_eig<R, false><<<dim3(ws.Pc, ngates), 256, sm_large, st>>>(s, ws, d_gates, ws.D, (int)sm_large);
+  k_refine<R><<<dim3(ws.Pc, ngates), 256, REFINE_SMEM, st>>>(s, ws, (int)REFINE_SMEM);
   if (ev) cudaEventRecord(ev[4], st);
-  k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, GRAM_FLOOR_FP64);
+  k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
   if (ev) cudaEventRecord(ev[5], st);
-  k_resplit<<<dim3(per, ngates), 256, ws.D * sizeof(double2), st>>>(s, ws, d_gates);
+  k_resplit<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
   if (ev) cudaEventRecord(ev[6], st);
-  if (nlaunch) *nlaunch += 6;
+}
+
+}  // namespace
+
+// One-time per-process setup (called outside any stream capture).
+cudaError_t gate_module_init() {
+  sm_count();
+  cudaError_t e = cudaFuncSetAttribute(k_eig<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)LARGE_SMEM_CAP);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eig<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LARGE_SMEM_CAP);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eig<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eig_smem_small<double>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_eig<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eig_smem_small<float>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_refine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)REFINE_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_refine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)REFINE_SMEM);
+  return e;
+}
+
+// stage_events (optional, 7 events): recorded before each stage launch and after the
+// last one, for per-stage timing.
+void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
+                  int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
+  if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev);
+  else launch_layer_t<float>(s, ws, d_gates, ngates, d_disc, st, ev);
+  if (nlaunch) *nlaunch += ws.D > SMALL_N ? 8 : 7;
 }
 
 void launch_phases(const MpoDev& s, const double* d_phase, cudaStream_t st) {

@@ -41,10 +41,13 @@ __global__ void k_init(MpoDev s, const double* __restrict__ r_all, const double*
   const double* r = r_all + (long long)inst * M;
   const double* eta = eta_all + (long long)inst * M;
 
+  // Every (c, cbar) quantity below is computed for c <= cbar and copied to the
+  // mirror pair (cbar, c), so the initial state is exactly ket/bra mirror-symmetric.
   // 1. per-mode lossy states and weights
   for (int idx = tid; idx < M * P; idx += nth) {
     int j = idx / P, p = idx % P;
     int n = pair_c(p, ncap), nb = pair_cb(p, ncap);
+    if (n > nb) continue;
     double val = 0.0;
     if (((n + nb) & 1) == 0) {
       double rr = r[j], et = eta[j];
@@ -68,6 +71,9 @@ __global__ void k_init(MpoDev s, const double* __restrict__ r_all, const double*
     }
     rho[idx] = val;
     wgt[idx] = val * val;
+    const long long mi = (long long)j * P + pair_mirror(p, ncap);
+    rho[mi] = val;
+    wgt[mi] = val * val;
   }
   __syncthreads();
 
@@ -80,32 +86,38 @@ __global__ void k_init(MpoDev s, const double* __restrict__ r_all, const double*
   for (int b = M - 1; b >= 0; --b) {
     for (int p = tid; p < P; p += nth) {
       int c = pair_c(p, ncap), cb = pair_cb(p, ncap);
+      if (c > cb) continue;
       double acc = 0.0;
       for (int n = 0; n <= c; ++n)
         for (int nb = 0; nb <= cb; ++nb)
           acc += wgt[(long long)b * P + n * q + nb] * R2[(long long)(b + 1) * P + (c - n) * q + (cb - nb)];
       R2[(long long)b * P + p] = acc;
+      R2[(long long)b * P + pair_mirror(p, ncap)] = acc;
     }
     __syncthreads();
   }
   for (int b = 0; b < M; ++b) {
     for (int p = tid; p < P; p += nth) {
       int c = pair_c(p, ncap), cb = pair_cb(p, ncap);
+      if (c > cb) continue;
       double acc = 0.0;
       for (int n = 0; n <= c; ++n)
         for (int nb = 0; nb <= cb; ++nb)
           acc += wgt[(long long)b * P + n * q + nb] * W2[(long long)b * P + (c - n) * q + (cb - nb)];
       W2[(long long)(b + 1) * P + p] = acc;
+      W2[(long long)(b + 1) * P + pair_mirror(p, ncap)] = acc;
     }
     __syncthreads();
   }
   for (int idx = tid; idx < (M + 1) * P; idx += nth) {
     int b = idx / P, p = idx % P;
     int c = pair_c(p, ncap), cb = pair_cb(p, ncap);
+    if (c > cb) continue;
     double acc = 0.0;
     for (int x = 0; x <= ncap - c; ++x)
       for (int xb = 0; xb <= ncap - cb; ++xb) acc += W2[(long long)b * P + x * q + xb];
     L2[idx] = acc;
+    L2[(long long)b * P + pair_mirror(p, ncap)] = acc;
   }
   // 3. trace normalisation T = Tr(P_cap (x) rho_j P_cap): diagonal convolution
   if (tid == 0) {

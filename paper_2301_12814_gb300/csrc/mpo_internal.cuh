@@ -43,7 +43,7 @@ struct MpoDev {
 };
 
 // algorithmic work counters (real flops of the executed form)
-enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_N };
+enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS, CTR_N };
 
 struct GateDesc {
   int inst, j, out, pad;
@@ -74,7 +74,7 @@ enum BlockField {
 
 enum SlotScalar {
   SS_NBLK = 0,  // canonical blocks (Pc, fixed)
-  SS_TTILES,    // total theta tiles
+  SS_TTILES,    // contraction work items: (row pair a, column pair b) segment pairs
   SS_GTILES,    // total gram tiles
   SS_NITEMS,    // resplit work items
   SS_STATUS,
@@ -98,6 +98,8 @@ struct SlotWS {
   int* perm;       // [S][capCand]  eigenvector column of the k-th largest
   double* dscal;   // [S][4]
   int* order;      // [S][capCand*2] candidate ids by rank (select)
+  int* items;      // [S][P*P] contraction items a*P + b
+  double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }
@@ -106,6 +108,11 @@ __host__ __device__ inline int pair_mirror(int p, int ncap) {
   return (p % (ncap + 1)) * (ncap + 1) + p / (ncap + 1);
 }
 __host__ __device__ inline int fock_off(int n) { return n * (n + 1) * (2 * n + 1) / 6; }
+// inverse of canon_pair for a pair with c <= cbar
+__host__ __device__ inline int canon_index(int m, int ncap) {
+  const int q = ncap + 1, c = m / q, cb = m % q;
+  return c * q - c * (c - 1) / 2 + (cb - c);
+}
 // canonical block t -> pair index m (pairs with c <= cbar, ascending pair index)
 __host__ __device__ inline int canon_pair(int t, int ncap) {
   int q = ncap + 1;

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from typing import Optional, Sequence
 
 import numpy as np
@@ -112,6 +113,7 @@ class Plan:
         _check(_lib().mpo_plan_mesh(owner._h, _ip_of(n_gates), _ip_of(k), _d(theta), _d(phi),
                                     _d(final_phase), ctypes.byref(h)), "mpo_plan_mesh")
         self._h = h
+        owner._plans.add(self)
         self.launches = int(_lib().mpo_plan_launches(h))
 
     def run(self) -> None:
@@ -131,9 +133,10 @@ class Plan:
         return {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
 
     def close(self) -> None:
-        if getattr(self, "_h", None):
+        # the owning handle frees its plans itself when it is destroyed first
+        if getattr(self, "_h", None) and getattr(self._owner, "_h", None):
             _lib().mpo_plan_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -163,6 +166,7 @@ class MPO:
             sp = int(getattr(stream, "cuda_stream", stream))
         prm = _Params(M=self.M, d=self.d, n_cap=0 if n_cap is None else int(n_cap), batch=self.batch,
                       prec=PRECISIONS[precision], chi_max=_ip_of(chis), cuda_stream=sp)
+        self._plans = weakref.WeakSet()
         h = _p()
         _check(lib.mpo_init_lossy_squeezed(ctypes.byref(h), ctypes.byref(prm), _d(r), _d(eta)),
                "mpo_init_lossy_squeezed")
@@ -232,6 +236,8 @@ class MPO:
 
     def close(self) -> None:
         if getattr(self, "_h", None):
+            for pl in list(getattr(self, "_plans", ())):
+                pl.close()
             _lib().mpo_destroy(self._h)
             self._h = None
 

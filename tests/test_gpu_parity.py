@@ -202,7 +202,7 @@ def test_large_workload_full_mesh_properties(lib, name):
     plan = G.plan_mesh([mesh.n_gates], mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
     plan.run()
     disc = plan.discarded()
-    assert np.all(disc >= 0) and np.all(disc < 1)
+    assert np.all(disc >= 0) and np.all(disc < 1), (disc.min(), disc.max())
     tr, n1, n2 = G.observables()
     assert 0.0 < tr[0] <= 1.0 + 1e-12
     assert np.all(n1 > 0) and np.all(n2 >= n1 - 1e-12)
@@ -252,3 +252,34 @@ def test_invalid_arguments_rejected_on_host(lib):
     with pytest.raises(lib.MPOError):
         G.apply_bs(0, float("nan"), 0.0)
     G.sync()   # the handle is still usable
+
+
+# Mixed path (FP32 contraction, Gram, eigensolver and back-multiplication; FP64
+# selection, lambda, entropy, state): errors against the FP64 oracle at the same chi.
+MIXED_BOUNDS = {"n_rel": 1e-4, "n2_rel": 1e-4, "S_abs": 1e-3, "tr_abs": 1e-4, "eps_rel": 1e-2}
+
+
+def mixed_errors(P, G):
+    tr, n1, n2 = P.observables()
+    gtr, gn1, gn2 = G.observables()
+    S = G.operator_entropy()[0][0]
+    return {"n_rel": float(np.max(np.abs(gn1[0] - n1) / n1)),
+            "n2_rel": float(np.max(np.abs(gn2[0] - n2) / n2)),
+            "S_abs": float(np.max(np.abs(S - np.array(P.entropy)))),
+            "tr_abs": float(abs(gtr[0] - tr))}
+
+
+@pytest.mark.parametrize("name,ngates", [("M16_d6_chi64", None), ("M32_d8_chi256", 24)])
+def test_mixed_precision_vs_oracle(lib, name, ngates):
+    wl = w.workload(name)
+    mesh = wl.mesh()
+    n = mesh.n_gates if ngates is None else ngates
+    P = oracle_run(wl, ngates=n, phases=(ngates is None))
+    G = gpu_handle(lib, wl, precision="mixed_tf32")
+    fp = mesh.final_phase if ngates is None else None
+    disc = G.sweep_mesh([n], mesh.k[:n], mesh.theta[:n], mesh.phi[:n], fp)
+    err = mixed_errors(P, G)
+    err["eps_rel"] = float(abs(np.sum(disc) - np.sum(P.discarded)) / max(np.sum(P.discarded), 1e-300))
+    print(name, "mixed errors", err)
+    for k, v in MIXED_BOUNDS.items():
+        assert err[k] <= v, (k, err[k], v)
