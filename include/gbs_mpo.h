@@ -121,17 +121,19 @@ mpo_status mpo_plan_discarded(mpo_plan p, double* discarded);
 /* Number of kernel launches one mpo_plan_run performs. */
 int mpo_plan_launches(mpo_plan p);
 /* Stages of one gate layer, in launch order (plus the final phase screen). */
-#define MPO_NSTAGES 7
+#define MPO_NSTAGES 8
 /* Replay the plan once without the graph, with a CUDA event between consecutive
  * stage launches on the handle's stream, and report per stage (setup, theta, gram,
- * eig, select, resplit, phases) the summed device time in ms, the launch count and
- * the real flops of the executed form (theta: complex MACs of Eq. `theta` over the
- * contracted blocks x 8; gram: upper triangle x 8 x inner size; eig: 54 x n per
- * applied Jacobi rotation; resplit: 8 x rows x cols per kept vector).  Each array
- * is [MPO_NSTAGES] host memory and nullable.  Same results as mpo_plan_run.
- * Synchronises. */
+ * eig, refine, select, resplit, phases) the summed device time in ms, the launch
+ * count and the real flops of the executed form (theta: complex MACs of Eq. `theta`
+ * over the contracted blocks x 8; gram: upper triangle x 8 x inner size; eig: per
+ * applied Jacobi rotation 54 n (complex) or 18 n (real); refine: W = Theta V plus
+ * 48 h + 24 n per applied one-sided rotation; resplit: element copies).  Each array
+ * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [3]): blocks
+ * factorised, two-sided Jacobi sweeps and one-sided refinement sweeps, summed over
+ * the replay.  Same results as mpo_plan_run.  Synchronises. */
 mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
-                            double* stage_flops);
+                            double* stage_flops, double* jacobi);
 void mpo_plan_destroy(mpo_plan p);
 
 /* Observables of every instance (once per mesh; trace environments):

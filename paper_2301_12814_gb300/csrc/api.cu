@@ -153,6 +153,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_or = take((size_t)S * w.capCand * 2 * sizeof(int));
   size_t o_it = take((size_t)S * w.P * w.P * sizeof(int));
   size_t o_w = take((size_t)S * w.capTheta * sizeof(double2));
+  size_t o_ns = take((size_t)S * w.capGram * sizeof(double2));
   void* buf = nullptr;
   CK(cudaMalloc(&buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
@@ -161,7 +162,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.coloff = (int*)(b + o_co); w.rowmap = (int*)(b + o_rm); w.colmap = (int*)(b + o_cm);
   w.fock = (double2*)(b + o_fk); w.theta = (double2*)(b + o_th); w.G = (double2*)(b + o_g);
   w.V = (double2*)(b + o_v); w.sval = (double*)(b + o_sv); w.perm = (int*)(b + o_pm);
-  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w);
+  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w); w.NS = (double2*)(b + o_ns);
   h->ws_buf = buf;
   h->ws = w;
   h->nslots = S;
@@ -467,12 +468,14 @@ mpo_status mpo_plan_discarded(mpo_plan p, double* discarded) {
 
 int mpo_plan_launches(mpo_plan p) { return p ? p->launches : 0; }
 
-mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, double* stage_flops) {
+mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, double* stage_flops,
+                            double* jacobi) {
   if (!p || !p->h) return MPO_ERR_ARG;
   mpo_handle h = p->h;
   if (h->poisoned) return MPO_ERR_POISONED;
   const int L = (int)p->layer_off.size();
-  std::vector<cudaEvent_t> ev((size_t)L * 7 + 2);
+  constexpr int NS = MPO_NSTAGES - 1;  // per-layer stages; the last stage is the phase screen
+  std::vector<cudaEvent_t> ev((size_t)L * (NS + 1) + 2);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   unsigned long long* d_ctr = nullptr;
   CK(cudaMallocAsync((void**)&d_ctr, CTR_N * sizeof(unsigned long long), h->stream));
@@ -481,34 +484,39 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   dv.ctr = d_ctr;
   for (int l = 0; l < L; ++l)
     launch_layer(dv, h->ws, p->d_gates + p->layer_off[l], p->layer_cnt[l], p->d_disc, h->prec,
-                 h->stream, nullptr, ev.data() + (size_t)l * 7);
-  CK(cudaEventRecord(ev[(size_t)L * 7], h->stream));
+                 h->stream, nullptr, ev.data() + (size_t)l * (NS + 1));
+  CK(cudaEventRecord(ev[(size_t)L * (NS + 1)], h->stream));
   if (p->d_phase) launch_phases(h->dev, p->d_phase, h->stream);
-  CK(cudaEventRecord(ev[(size_t)L * 7 + 1], h->stream));
+  CK(cudaEventRecord(ev[(size_t)L * (NS + 1) + 1], h->stream));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   double ms[MPO_NSTAGES] = {0};
   for (int l = 0; l < L; ++l)
-    for (int st = 0; st < 6; ++st) {
+    for (int st = 0; st < NS; ++st) {
       float t = 0.f;
-      CK(cudaEventElapsedTime(&t, ev[(size_t)l * 7 + st], ev[(size_t)l * 7 + st + 1]));
+      CK(cudaEventElapsedTime(&t, ev[(size_t)l * (NS + 1) + st], ev[(size_t)l * (NS + 1) + st + 1]));
       ms[st] += t;
     }
   float tp = 0.f;
-  CK(cudaEventElapsedTime(&tp, ev[(size_t)L * 7], ev[(size_t)L * 7 + 1]));
-  ms[6] = tp;
+  CK(cudaEventElapsedTime(&tp, ev[(size_t)L * (NS + 1)], ev[(size_t)L * (NS + 1) + 1]));
+  ms[NS] = tp;
   for (auto& e : ev) cudaEventDestroy(e);
   unsigned long long ctr[CTR_N];
   CK(cudaMemcpyAsync(ctr, d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   cudaFreeAsync(d_ctr, h->stream);
-  // stage order: setup, theta, gram, eig, select, resplit, phases
+  // stage order: setup, theta, gram, eig, refine, select, resplit, phases
   const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], (double)ctr[CTR_EIG],
-                                  0.0, (double)ctr[CTR_RESPLIT], 0.0};
+                                  (double)ctr[CTR_REFINE], 0.0, (double)ctr[CTR_RESPLIT], 0.0};
   for (int st = 0; st < MPO_NSTAGES; ++st) {
     if (stage_ms) stage_ms[st] = ms[st];
-    if (stage_launches) stage_launches[st] = st < 6 ? L : (p->d_phase ? 1 : 0);
+    if (stage_launches) stage_launches[st] = st < NS ? L : (p->d_phase ? 1 : 0);
     if (stage_flops) stage_flops[st] = fl[st];
+  }
+  if (jacobi) {
+    jacobi[0] = (double)ctr[CTR_EIGBLK];
+    jacobi[1] = (double)ctr[CTR_SWEEPS];
+    jacobi[2] = (double)ctr[CTR_RSWEEPS];
   }
   return poll_error(h);
 }

@@ -23,15 +23,17 @@
 //   formed once and mixed into every canonical new centre m between a and b with the
 //   weight u(a, b, c, m).  Eq. `theta` evaluates the same sum per m; factoring P_c out
 //   removes the repeated inner products and all padding of small segments.
-// * The SVD is a Gram matrix (smaller side) plus a parallel-order cyclic Jacobi
-//   eigensolver, one CTA per block, in two size classes (n <= 32: small CTAs, many
-//   per SM; larger: up to 200 KB of shared memory, global memory beyond that).
-//   Singular values below the Gram accuracy floor are dropped.
+// * The SVD: a Gram matrix (smaller side) and a parallel-order cyclic Jacobi
+//   eigensolver, both in FP32 on every path, give a starting basis; a one-sided
+//   Jacobi refinement in the path's precision (FP64 on the FP64 path) then iterates
+//   to convergence on W = Theta V.  The eigensolver runs one CTA per block in two
+//   size classes (n <= 32: small CTAs, many per SM; larger: up to 200 KB of shared
+//   memory, global memory beyond that).
 // * The beam-splitter Fock blocks are built on the device by the creation-operator
 //   recurrence U|j, n-j> = (S11 a1^dag + S21 a2^dag) U|j-1, n-j> / sqrt(j).
-// * Precision: R = double (FP64 path) or float (mixed path: contraction, Gram,
-//   eigensolver and back-multiplication in FP32; selection, lambda, discarded weight,
-//   entropy and the stored state in FP64).
+// * Precision: R = double (FP64 path) or float (mixed path: contraction and
+//   refinement in FP32); selection, lambda, discarded weight, entropy and the stored
+//   state are FP64 on both.
 // * The Gram eigenvectors seed a one-sided Jacobi refinement on W = Theta V, which
 //   makes the singular values and vectors accurate relative to s_max (not s_max^2)
 //   and yields both factors, so the re-split is a scaled copy.
@@ -116,7 +118,7 @@ template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return ma
 struct Slot {
   int* blk; int* scal; int* rowoff; int* coloff; int* rowmap; int* colmap;
   double2* fock; void* theta; void* G; void* V; double* sval; int* perm;
-  double* dscal; int* order; int* items; void* W;
+  double* dscal; int* order; int* items; void* W; void* NS;
   int Pc;
   __device__ __forceinline__ int& f(int field, int t) const { return blk[field * (Pc + 1) + t]; }
 };
@@ -140,6 +142,7 @@ __device__ __forceinline__ Slot get_slot(const SlotWS& ws, int s) {
   sl.order = ws.order + (long long)s * ws.capCand * 2;
   sl.items = ws.items + (long long)s * ws.P * ws.P;
   sl.W = ws.W + (long long)s * ws.capTheta;
+  sl.NS = ws.NS + (long long)s * ws.capGram;
   return sl;
 }
 
@@ -456,10 +459,13 @@ __global__ void __launch_bounds__(256) k_theta(MpoDev st, SlotWS ws, const GateD
 }
 
 // ---------------------------------------------------------------- k_gram
-// Upper-triangular 16 x 16 tiles of G = Theta Theta^dag (side 0) or Theta^dag Theta.
-template <typename R>
+// Upper-triangular 16 x 16 tiles of G = Theta Theta^dag (side 0) or Theta^dag Theta,
+// in FP32: the Gram eigenvectors only seed the one-sided refinement (k_refine),
+// which iterates to the accuracy of the path's own precision from any complete basis.
+template <typename RT>
 __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr) {
-  typedef typename Prec<R>::C C;
+  typedef typename Prec<RT>::C CT;
+  typedef float2 C;
   const int s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
@@ -469,14 +475,14 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
   __shared__ int gpre[MPO_PC_MAX + 1];
   for (int t = threadIdx.x; t <= Pc; t += blockDim.x) gpre[t] = sl.f(BF_GT, t);
   __syncthreads();
-  const C* ThAll = reinterpret_cast<const C*>(sl.theta);
+  const CT* ThAll = reinterpret_cast<const CT*>(sl.theta);
   C* GAll = reinterpret_cast<C*>(sl.G);
   const int total = sl.scal[SS_GTILES];
   unsigned long long flops = 0;
   for (int z = blockIdx.x; z < total; z += gridDim.x) {
     const int t = find_block(gpre, Pc + 1, z);
     const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), gg = sl.f(BF_G, t), side = sl.f(BF_SIDE, t);
-    const C* Th = ThAll + sl.f(BF_TOFF, t);
+    const CT* Th = ThAll + sl.f(BF_TOFF, t);
     C* Gm = GAll + sl.f(BF_GOFF, t);
     const int nt = (gg + TILE - 1) / TILE;
     int rem = z - gpre[t], ti = 0;
@@ -488,12 +494,12 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
       __syncthreads();
       if (side == 0) {
         int ia = ti * TILE + ty, ib = tj * TILE + ty, kk = k0 + tx;
-        As[ty][tx] = (ia < gg && kk < K) ? Th[(long long)ia * c + kk] : zero_e<C>();
-        Bs[ty][tx] = (ib < gg && kk < K) ? Th[(long long)ib * c + kk] : zero_e<C>();
+        As[ty][tx] = (ia < gg && kk < K) ? cvt<C>(to_d2(Th[(long long)ia * c + kk])) : zero_e<C>();
+        Bs[ty][tx] = (ib < gg && kk < K) ? cvt<C>(to_d2(Th[(long long)ib * c + kk])) : zero_e<C>();
       } else {
         int kr = k0 + ty, ja = ti * TILE + tx, jb = tj * TILE + tx;
-        As[ty][tx] = (kr < K && ja < gg) ? Th[(long long)kr * c + ja] : zero_e<C>();
-        Bs[ty][tx] = (kr < K && jb < gg) ? Th[(long long)kr * c + jb] : zero_e<C>();
+        As[ty][tx] = (kr < K && ja < gg) ? cvt<C>(to_d2(Th[(long long)kr * c + ja])) : zero_e<C>();
+        Bs[ty][tx] = (kr < K && jb < gg) ? cvt<C>(to_d2(Th[(long long)kr * c + jb])) : zero_e<C>();
       }
       __syncthreads();
       const int kn = (K - k0) < TILE ? (K - k0) : TILE;
@@ -980,15 +986,55 @@ __global__ void __launch_bounds__(256) k_refine(MpoDev st, SlotWS ws, int smem_b
   size_t off = 16 + (((size_t)nn * sizeof(R) + 15) & ~(size_t)15);
   const bool in_smem = off + ((size_t)h * n + (size_t)n * n) * sizeof(C) <= (size_t)smem_bytes;
   const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
-  const C* V0 = reinterpret_cast<const C*>(sl.V) + sl.f(BF_GOFF, t);   // row-major from k_eig
+  const float2* V0 = reinterpret_cast<const float2*>(sl.V) + sl.f(BF_GOFF, t);  // row-major FP32 seed
   C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);
   C* gVc = reinterpret_cast<C*>(sl.G) + sl.f(BF_GOFF, t);             // the Gram is dead now
   C* W = in_smem ? reinterpret_cast<C*>(smem + off) : gW;
   C* Vc = in_smem ? W + (size_t)h * n : gVc;
   if (tid == 0) { flags[0] = 0; flags[1] = 0; }
-  for (int e = tid; e < n * n; e += nth) {  // column-major copy of V
-    const int k = e / n, i = e % n;
-    Vc[e] = V0[(long long)i * n + k];
+  if (sizeof(R) == 8) {
+    // The FP32 seed is unitary only to ~1e-7 and the rotations below keep any
+    // non-unitarity, so it is first orthonormalised in FP64 by two Newton-Schulz
+    // steps V <- V (3 I - V^dag V) / 2 (error delta -> ~delta^2 per step), in global
+    // scratch: S = V^dag V in the slot's NS buffer, V S in the W buffer (free until W
+    // is formed below).
+    C* S = reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t);
+    C* T = gW;
+    for (int e = tid; e < n * n; e += nth) T[e] = cvt<C>(to_d2(V0[(long long)(e % n) * n + e / n]));
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      for (int e = tid; e < n * n; e += nth) {  // S[a][b] = v_a^dag v_b (column-major)
+        const int b = e / n, a = e % n;
+        C acc = zero_e<C>();
+        for (int i = 0; i < n; ++i) cfma_cj(acc, gVc[(long long)a * n + i], gVc[(long long)b * n + i]);
+        S[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) {  // T[:, b] = sum_a V[:, a] (3 delta_ab - S_ab) / 2
+        const int b = e / n, i = e % n;
+        C acc = zero_e<C>();
+        for (int a = 0; a < n; ++a) {
+          C w = S[(long long)b * n + a];
+          w.x = (a == b ? (R)1.5 : (R)0) - (R)0.5 * w.x;
+          w.y = -(R)0.5 * w.y;
+          cfma(acc, gVc[(long long)a * n + i], w);
+        }
+        T[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
+      __syncthreads();
+    }
+    if (in_smem) {
+      for (int e = tid; e < n * n; e += nth) Vc[e] = gVc[e];
+    }
+  } else {
+    for (int e = tid; e < n * n; e += nth) {  // column-major copy of V
+      const int k = e / n, i = e % n;
+      Vc[e] = cvt<C>(to_d2(V0[(long long)i * n + k]));
+    }
   }
   __syncthreads();
   for (int e = tid; e < h * n; e += nth) {
@@ -1016,6 +1062,9 @@ __global__ void __launch_bounds__(256) k_refine(MpoDev st, SlotWS ws, int smem_b
   for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
   __syncthreads();
   const R tol_abs = Prec<R>::os_abs * mx;
+  // columns at or below the selection floor are dropped anyway: rotating them only
+  // churns rounding noise, so pairs involving one are skipped
+  const R col_floor = (R)Prec<R>::floor * mx;
   const int np = n + (n & 1), half = np / 2;
   int sweep = 0;
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
@@ -1049,7 +1098,8 @@ __global__ void __launch_bounds__(256) k_refine(MpoDev st, SlotWS ws, int smem_b
         // that phase would break the symmetry, so the rotation is kept real
         if (selfm) ga.y = 0;
         const R hh = absv(ga);
-        if (!(hh > Prec<R>::os_rel * sqrt(al * be) && hh > tol_abs)) continue;  // warp-uniform
+        if (!(hh > Prec<R>::os_rel * sqrt(al * be) && hh > tol_abs && al > col_floor && be > col_floor))
+          continue;  // warp-uniform
         const R tau = (be - al) / (2 * hh);
         const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
         const R cs = (R)1 / sqrt((R)1 + tt * tt), sn = tt * cs;
@@ -1236,8 +1286,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   int per = (4 * sms + ngates - 1) / ngates;
   if (per < 1) per = 1;
   if (per > 4096) per = 4096;
-  const size_t sm_small = eig_smem_small<R>();
-  const size_t sm_large = eig_smem_large<R>(ws.D);
+  const size_t sm_small = eig_smem_small<float>();
+  const size_t sm_large = eig_smem_large<float>(ws.D);
   if (ev) cudaEventRecord(ev[0], st);
   k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates);
   if (ev) cudaEventRecord(ev[1], st);
@@ -1245,15 +1295,16 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) cudaEventRecord(ev[2], st);
   k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
   if (ev) cudaEventRecord(ev[3], st);
-  k_eig<R, true><<<dim3(ws.Pc, ngates), 128, sm_small, st>>>(s, ws, d_gates, SMALL_N, (int)sm_small);
+  k_eig<float, true><<<dim3(ws.Pc, ngates), 128, sm_small, st>>>(s, ws, d_gates, SMALL_N, (int)sm_small);
   if (ws.D > SMALL_N)
-    k_eig<R, false><<<dim3(ws.Pc, ngates), 256, sm_large, st>>>(s, ws, d_gates, ws.D, (int)sm_large);
-  k_refine<R><<<dim3(ws.Pc, ngates), 256, REFINE_SMEM, st>>>(s, ws, (int)REFINE_SMEM);
+    k_eig<float, false><<<dim3(ws.Pc, ngates), 256, sm_large, st>>>(s, ws, d_gates, ws.D, (int)sm_large);
   if (ev) cudaEventRecord(ev[4], st);
-  k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
+  k_refine<R><<<dim3(ws.Pc, ngates), 256, REFINE_SMEM, st>>>(s, ws, (int)REFINE_SMEM);
   if (ev) cudaEventRecord(ev[5], st);
-  k_resplit<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
+  k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
   if (ev) cudaEventRecord(ev[6], st);
+  k_resplit<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
+  if (ev) cudaEventRecord(ev[7], st);
 }
 
 }  // namespace
@@ -1261,13 +1312,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
 // One-time per-process setup (called outside any stream capture).
 cudaError_t gate_module_init() {
   sm_count();
-  cudaError_t e = cudaFuncSetAttribute(k_eig<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_eig<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)LARGE_SMEM_CAP);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eig<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LARGE_SMEM_CAP);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eig<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)eig_smem_small<double>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_eig<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)eig_smem_small<float>());
@@ -1278,8 +1324,8 @@ cudaError_t gate_module_init() {
   return e;
 }
 
-// stage_events (optional, 7 events): recorded before each stage launch and after the
-// last one, for per-stage timing.
+// stage_events (optional, 8 events): recorded before each stage launch and after the
+// last one, for per-stage timing (setup, theta, gram, eig, refine, select, resplit).
 void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
                   int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
   if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev);

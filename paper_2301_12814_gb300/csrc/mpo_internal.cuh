@@ -100,6 +100,7 @@ struct SlotWS {
   int* order;      // [S][capCand*2] candidate ids by rank (select)
   int* items;      // [S][P*P] contraction items a*P + b
   double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
+  double2* NS;     // [S][capGram] Newton-Schulz scratch V^dag V of the FP64 refinement
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }

@@ -68,7 +68,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_plan_run": (_i, [_p]),
         "mpo_plan_discarded": (_i, [_p, _dp]),
         "mpo_plan_launches": (_i, [_p]),
-        "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp]),
+        "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp, _dp]),
         "mpo_plan_destroy": (None, [_p]),
         "mpo_observables": (_i, [_p, _dp, _dp, _dp, _i]),
         "mpo_operator_entropy": (_i, [_p, _dp, _dp, _dp]),
@@ -124,13 +124,17 @@ class Plan:
         _check(_lib().mpo_plan_discarded(self._h, _d(out)), "mpo_plan_discarded")
         return out[:self.n_total]
 
-    STAGES = ("setup", "theta", "gram", "eig", "select", "resplit", "phases")
+    STAGES = ("setup", "theta", "gram", "eig", "refine", "select", "resplit", "phases")
 
-    def profile(self):
-        """One instrumented replay: {stage: (ms, launches, flops)}."""
-        ms = np.zeros(7); nl = np.zeros(7, dtype=np.int32); fl = np.zeros(7)
-        _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl)), "mpo_plan_profile")
-        return {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
+    def profile(self, with_jacobi: bool = False):
+        """One instrumented replay: {stage: (ms, launches, flops)} (and, if asked,
+        {blocks, two-sided sweeps, one-sided sweeps})."""
+        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(3)
+        _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl), _d(jb)), "mpo_plan_profile")
+        out = {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
+        if with_jacobi:
+            return out, {"blocks": int(jb[0]), "sweeps": int(jb[1]), "refine_sweeps": int(jb[2])}
+        return out
 
     def close(self) -> None:
         # the owning handle frees its plans itself when it is destroyed first
