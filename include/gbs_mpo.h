@@ -168,6 +168,36 @@ mpo_status mpo_sync(mpo_handle h);
 void mpo_destroy(mpo_handle h);
 const char* mpo_status_string(mpo_status s);
 
+/* Observables of one MPO held in buffers the caller owns, with no allocation.
+ * The paper has no counterpart: this is a library-interface addition for callers
+ * that cannot allocate device memory when they need the observables -- code inside
+ * a host application or framework that owns all device memory (its own pool
+ * allocator or a fixed budget) and forbids direct cudaMalloc/cudaFree, which also
+ * synchronise the device.  It runs the same trace-environment kernel as
+ * mpo_observables; its scratch (2 (M+1) D complex doubles) is a file-scope device
+ * array of 65536 complex doubles (1 MiB) that every GPU loading the library holds
+ * until the process exits.  Larger M or D return MPO_ERR_CAPACITY.
+ *   M, n_cap, D  modes, charge cap (<= 15), bond capacity (row stride of Gamma)
+ *   chi     [M+1]            device: bond dimensions
+ *   charge  [(M+1)*D]        device: pair index c*(n_cap+1)+cbar of each bond index,
+ *                            ascending within a bond
+ *   segoff  [(M+1)*P1]       device: per bond P1 = (n_cap+1)^2 + 1 segment offsets
+ *                            (indices of pair p occupy [segoff[p], segoff[p+1]))
+ *   lam     [(M+1)*D]        device: Vidal weights
+ *   gam     [M*D*D]          device: complex128 (re, im) Gamma_j, row-major D x D,
+ *                            rows = bond j, columns = bond j+1 (the handle's layout)
+ *   out     [3M+2]           device: Tr rho, <n_j> Tr rho (M), <n_j^2> Tr rho (M),
+ *                            sum lambda^2 per bond (M+1) -- moments not divided by Tr
+ *   cuda_stream              stream to run on (NULL = legacy default)
+ * Asynchronous: out is ready when the stream reaches this point.  The first call on
+ * a device looks up the scratch array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call
+ * shares the one scratch array, which keeps the last call's contents (nothing in it
+ * needs to start at zero): calls that overlap on the GPU race with each other. */
+mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const int* charge,
+                                  const int* segoff, const double* lam, const void* gam,
+                                  double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

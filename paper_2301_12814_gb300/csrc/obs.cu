@@ -8,6 +8,9 @@
 //   F_M = 1,         F_j(a)     = sum_b Gamma_j[a, b] lambda_{j+1}(b) F_{j+1}(b)
 //   Tr rho = E_M,    <n_j^p> Tr rho = sum_{a,b} E_j(a) Gamma_j[a, b] i^p lambda_{j+1}(b) F_{j+1}(b)
 // Sums run over segments: the partners of b are the pairs (c_b + i, cbar_b + i).
+#include <mutex>
+
+#include "../../include/gbs_mpo.h"
 #include "mpo_internal.cuh"
 
 namespace {
@@ -122,4 +125,66 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
 
 void launch_observables(const MpoDev& s, double2* scratch, double* out, cudaStream_t st) {
   k_obs<<<s.B, 256, 0, st>>>(s, scratch, out);
+}
+
+// ---------------------------------------------------------------------------
+// Observables without any allocation (mpo_observables_static in gbs_mpo.h).
+//
+// Some callers cannot allocate device memory at the point where they need the
+// observables: a host application or framework that owns all device memory
+// (its own pool allocator or a fixed, pre-partitioned budget) and forbids direct
+// cudaMalloc/cudaFree, for instance because those calls synchronise the device
+// and would stall its other work.  This variant runs the same k_obs kernel on a
+// single MPO held in buffers the caller already owns; the only scratch it needs,
+// the left and right trace environments (2 (M+1) D complex values), lives in the
+// file-scope array below.  Every GPU that loads the library keeps this array
+// (MPO_STATIC_SCRATCH_ELEMS complex doubles, 1 MiB) until the process exits.
+#define MPO_STATIC_SCRATCH_ELEMS (1 << 16)
+static __device__ __align__(256) double2 g_obs_scratch[MPO_STATIC_SCRATCH_ELEMS];
+
+namespace {
+// Device address of g_obs_scratch per device, looked up once per device (with that
+// device current) by cudaGetSymbolAddress: in host code the symbol's name is only a
+// host-side stand-in, never a device address.
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double2* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+cudaError_t static_scratch(double2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_obs_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<double2*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const int* charge,
+                                             const int* segoff, const double* lam, const void* gam,
+                                             double* out, void* cuda_stream) {
+  if (M < 2 || M > 256 || n_cap < 1 || n_cap > MPO_NCAP_MAX || D < 1) return MPO_ERR_ARG;
+  if (!chi || !charge || !segoff || !lam || !gam || !out) return MPO_ERR_ARG;
+  if (2ll * (M + 1) * D > MPO_STATIC_SCRATCH_ELEMS) return MPO_ERR_CAPACITY;
+  double2* scratch = nullptr;
+  cudaError_t e = static_scratch(&scratch);
+  if (e != cudaSuccess) return MPO_ERR_CUDA;
+  MpoDev s{};
+  s.B = 1; s.M = M; s.ncap = n_cap; s.P = (n_cap + 1) * (n_cap + 1); s.D = D;
+  s.chi = const_cast<int*>(chi);
+  s.charge = const_cast<int*>(charge);
+  s.segoff = const_cast<int*>(segoff);
+  s.lam = const_cast<double*>(lam);
+  s.gam = static_cast<double2*>(const_cast<void*>(gam));
+  // nothing in the scratch has to start at zero: k_obs writes every environment
+  // entry before it reads it
+  launch_observables(s, scratch, out, static_cast<cudaStream_t>(cuda_stream));
+  return cudaGetLastError() == cudaSuccess ? MPO_OK : MPO_ERR_CUDA;
 }

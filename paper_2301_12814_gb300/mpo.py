@@ -25,7 +25,7 @@ EXPORTS = [
     "mpo_plan_run", "mpo_plan_discarded", "mpo_plan_launches", "mpo_plan_profile",
     "mpo_plan_destroy",
     "mpo_observables", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
-    "mpo_sync", "mpo_destroy", "mpo_status_string",
+    "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static",
 ]
 
 
@@ -77,6 +77,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_sync": (_i, [_p]),
         "mpo_destroy": (None, [_p]),
         "mpo_status_string": (ctypes.c_char_p, [_i]),
+        "mpo_observables_static": (_i, [_i, _i, _i, _p, _p, _p, _p, _p, _p, _p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
