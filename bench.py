@@ -237,9 +237,11 @@ def run_native(args, ws, rank, local):
             torch.distributed.destroy_process_group()
         return
     # roofline on the dominant stage; its arithmetic pipe sets the peak (SIMT FP64 or FP32)
-    stage = max(("theta", "gram", "eig", "refine", "resplit"), key=lambda s: prof[s][0])
+    stage = max(("theta", "gram", "svd", "resplit"), key=lambda s: prof[s][0])
     ms_s, nl_s, fl_s = prof[stage]
-    fp64_stage = prec == "fp64" and stage in ("theta", "refine")
+    fp64_stage = prec == "fp64" and stage in ("theta", "svd")
+    if stage == "svd" and prec == "fp64":
+        fl_s = jac["refine_flops"]  # the FP64 part; the FP32 seed is reported beside it
     peak = FP64_PEAK_TFLOPS if fp64_stage else FP32_PEAK_TFLOPS
     achieved = fl_s / (ms_s / 1e3) / 1e12 if ms_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": f"k_{stage}", "achieved": achieved, "peak": peak,
@@ -279,7 +281,8 @@ def run_native(args, ws, rank, local):
         "stages_ms": {s: round(v[0], 4) for s, v in prof.items()},
         "stages_gflop": {s: round(v[2] / 1e9, 4) for s, v in prof.items() if v[2] > 0},
         "jacobi": {"blocks": jac["blocks"], "sweeps_per_block": jac["sweeps"] / max(1, jac["blocks"]),
-                   "refine_sweeps_per_block": jac["refine_sweeps"] / max(1, jac["blocks"])},
+                   "refine_sweeps_per_block": jac["refine_sweeps"] / max(1, jac["blocks"]),
+                   "seed_gflop_fp32": jac["seed_flops"] / 1e9, "refine_gflop": jac["refine_flops"] / 1e9},
         "wall_s": wall,
         "observables": {"trace": float(tr[0]), "discarded_sum": float(np.sum(disc[:n_gates[0]])),
                         "S_max": float(smax[0])},

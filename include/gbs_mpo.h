@@ -124,14 +124,16 @@ int mpo_plan_launches(mpo_plan p);
 #define MPO_NSTAGES 8
 /* Replay the plan once without the graph, with a CUDA event between consecutive
  * stage launches on the handle's stream, and report per stage (setup, theta, gram,
- * eig, refine, select, resplit, phases) the summed device time in ms, the launch
+ * order, svd, select, resplit, phases) the summed device time in ms, the launch
  * count and the real flops of the executed form (theta: complex MACs of Eq. `theta`
- * over the contracted blocks x 8; gram: upper triangle x 8 x inner size; eig: per
- * applied Jacobi rotation 54 n (complex) or 18 n (real); refine: W = Theta V plus
- * 48 h + 24 n per applied one-sided rotation; resplit: element copies).  Each array
- * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [3]): blocks
- * factorised, two-sided Jacobi sweeps and one-sided refinement sweeps, summed over
- * the replay.  Same results as mpo_plan_run.  Synchronises. */
+ * over the contracted blocks x 8; gram: upper triangle x 8 x inner size; svd: FP32
+ * seed Jacobi, per applied rotation 54 n (complex) or 18 n (real), plus the
+ * refinement, W = Theta V and 48 h + 24 n per applied one-sided rotation, in the
+ * path's precision; resplit: element copies).  Each array
+ * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [5]): blocks
+ * factorised, two-sided (seed) Jacobi sweeps, one-sided refinement sweeps, seed
+ * flops (FP32) and refinement flops (path precision), summed over the replay.
+ * Same results as mpo_plan_run.  Synchronises. */
 mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
                             double* stage_flops, double* jacobi);
 void mpo_plan_destroy(mpo_plan p);

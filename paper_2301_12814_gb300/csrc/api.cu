@@ -130,7 +130,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
   w.capTheta = (long long)h->Pc * D * D;
-  // per-slot budget for Theta/W/G/V (4 complex arrays): 2 GiB
+  // per-slot budget for each of the Theta-sized complex arrays (Theta, W, G, V, NS, VC): 512 MiB
   const long long budget = (2ll << 30) / (4 * (long long)sizeof(double2));
   if (w.capTheta > budget) w.capTheta = budget;
   w.capGram = w.capTheta;
@@ -154,6 +154,9 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_it = take((size_t)S * w.P * w.P * sizeof(int));
   size_t o_w = take((size_t)S * w.capTheta * sizeof(double2));
   size_t o_ns = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_vc = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_ls = take((size_t)S * w.Pc * sizeof(int));
+  size_t o_ct = take(4 * sizeof(int));
   void* buf = nullptr;
   CK(cudaMalloc(&buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
@@ -162,7 +165,8 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.coloff = (int*)(b + o_co); w.rowmap = (int*)(b + o_rm); w.colmap = (int*)(b + o_cm);
   w.fock = (double2*)(b + o_fk); w.theta = (double2*)(b + o_th); w.G = (double2*)(b + o_g);
   w.V = (double2*)(b + o_v); w.sval = (double*)(b + o_sv); w.perm = (int*)(b + o_pm);
-  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w); w.NS = (double2*)(b + o_ns);
+  w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w); w.NS = (double2*)(b + o_ns); w.VC = (double2*)(b + o_vc);
+  w.list = (int*)(b + o_ls); w.counter = (int*)(b + o_ct);
   h->ws_buf = buf;
   h->ws = w;
   h->nslots = S;
@@ -505,9 +509,9 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   CK(cudaMemcpyAsync(ctr, d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   cudaFreeAsync(d_ctr, h->stream);
-  // stage order: setup, theta, gram, eig, refine, select, resplit, phases
-  const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], (double)ctr[CTR_EIG],
-                                  (double)ctr[CTR_REFINE], 0.0, (double)ctr[CTR_RESPLIT], 0.0};
+  // stage order: setup, theta, gram, order, svd, select, resplit, phases
+  const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], 0.0,
+                                  (double)(ctr[CTR_EIG] + ctr[CTR_REFINE]), 0.0, (double)ctr[CTR_RESPLIT], 0.0};
   for (int st = 0; st < MPO_NSTAGES; ++st) {
     if (stage_ms) stage_ms[st] = ms[st];
     if (stage_launches) stage_launches[st] = st < NS ? L : (p->d_phase ? 1 : 0);
@@ -517,6 +521,8 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
     jacobi[0] = (double)ctr[CTR_EIGBLK];
     jacobi[1] = (double)ctr[CTR_SWEEPS];
     jacobi[2] = (double)ctr[CTR_RSWEEPS];
+    jacobi[3] = (double)ctr[CTR_EIG];
+    jacobi[4] = (double)ctr[CTR_REFINE];
   }
   return poll_error(h);
 }

@@ -26,9 +26,9 @@
 // * The SVD: a Gram matrix (smaller side) and a parallel-order cyclic Jacobi
 //   eigensolver, both in FP32 on every path, give a starting basis; a one-sided
 //   Jacobi refinement in the path's precision (FP64 on the FP64 path) then iterates
-//   to convergence on W = Theta V.  The eigensolver runs one CTA per block in two
-//   size classes (n <= 32: small CTAs, many per SM; larger: up to 200 KB of shared
-//   memory, global memory beyond that).
+//   to convergence on W = Theta V.  Both run in k_svd: one persistent CTA per SM
+//   takes the layer's blocks longest first and keeps each block in 200 KB of shared
+//   memory when it fits.
 // * The beam-splitter Fock blocks are built on the device by the creation-operator
 //   recurrence U|j, n-j> = (S11 a1^dag + S21 a2^dag) U|j-1, n-j> / sqrt(j).
 // * Precision: R = double (FP64 path) or float (mixed path: contraction and
@@ -37,15 +37,13 @@
 // * The Gram eigenvectors seed a one-sided Jacobi refinement on W = Theta V, which
 //   makes the singular values and vectors accurate relative to s_max (not s_max^2)
 //   and yields both factors, so the re-split is a scaled copy.
-// Stages: k_setup -> k_theta -> k_gram -> k_eig (small, large) -> k_refine ->
-// k_select -> k_resplit.
+// Stages: k_setup -> k_theta -> k_gram -> k_order -> k_svd -> k_select -> k_resplit.
 #include "mpo_internal.cuh"
 
 namespace {
 
 constexpr int TILE = 16;
 constexpr int MCH = 8;        // new-centre charges mixed per pass of the contraction
-constexpr int SMALL_N = 32;   // eigen blocks up to this size use the small-CTA kernel
 constexpr double TIE_REL = 1e-9;
 constexpr int JACOBI_MAX_SWEEPS = 60;
 
@@ -118,7 +116,7 @@ template <> __device__ __forceinline__ float2 cvt<float2>(double2 a) { return ma
 struct Slot {
   int* blk; int* scal; int* rowoff; int* coloff; int* rowmap; int* colmap;
   double2* fock; void* theta; void* G; void* V; double* sval; int* perm;
-  double* dscal; int* order; int* items; void* W; void* NS;
+  double* dscal; int* order; int* items; void* W; void* NS; void* VC;
   int Pc;
   __device__ __forceinline__ int& f(int field, int t) const { return blk[field * (Pc + 1) + t]; }
 };
@@ -143,6 +141,7 @@ __device__ __forceinline__ Slot get_slot(const SlotWS& ws, int s) {
   sl.items = ws.items + (long long)s * ws.P * ws.P;
   sl.W = ws.W + (long long)s * ws.capTheta;
   sl.NS = ws.NS + (long long)s * ws.capGram;
+  sl.VC = ws.VC + (long long)s * ws.capGram;
   return sl;
 }
 
@@ -535,7 +534,16 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
 // R = [[c, s], [-s, c]] with t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
 // tau = (G_qq - G_pp) / (2|g|) annihilates it, and J = D R is applied as
 // G <- J^dag G J, V <- V J.  E = R for real symmetric, E = complex for Hermitian.
+// The pairs of a round are disjoint, so a round is processed in chunks of at most
+// PAIR_CHUNK pairs: a chunk's 2x2 sub-blocks are untouched by the other chunks.
 template <typename R, typename E> struct Rot { int p, q; R c, s; E e; };
+constexpr int PAIR_CHUNK = 256;
+
+__device__ __forceinline__ void circle_pair(int rnd, int k, int np, int& p, int& q) {
+  if (k == 0) { p = rnd; q = np - 1; }
+  else { p = (rnd + k) % (np - 1); q = (rnd - k + np - 1) % (np - 1); }
+  if (p > q) { const int t = p; p = q; q = t; }
+}
 
 template <typename R, typename E>
 __device__ int jacobi(E* A, E* V, int n, Rot<R, E>* rot, int* flags, R tol_rel, R tol_abs_rel) {
@@ -552,55 +560,165 @@ __device__ int jacobi(E* A, E* V, int n, Rot<R, E>* rot, int* flags, R tol_rel, 
     if (tid == 0) flags[0] = 0;
     __syncthreads();
     for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int k = tid; k < half; k += nth) {
-        int p, qq;
-        if (k == 0) { p = rnd; qq = np - 1; }
-        else { p = (rnd + k) % (np - 1); qq = (rnd - k + np - 1) % (np - 1); }
-        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
-        Rot<R, E> rp;
-        rp.p = p; rp.q = -1; rp.c = 1; rp.s = 0; rp.e = unit_e<E>();
-        if (qq < n) {
-          const R a = re(A[(long long)p * n + p]), b = re(A[(long long)qq * n + qq]);
-          const E gpq = A[(long long)p * n + qq];
-          const R hh = absv(gpq);
-          if (hh > tol_rel * sqrt(fabs(a * b)) && hh > tol_abs) {
-            const R tau = (b - a) / (2 * hh);
-            const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
-            rp.q = qq;
-            rp.c = (R)1 / sqrt((R)1 + tt * tt);
-            rp.s = tt * rp.c;
-            rp.e = divr<E, R>(gpq, hh);
-            flags[0] = 1;
-            atomicAdd(&flags[1], 1);
+      for (int c0 = 0; c0 < half; c0 += PAIR_CHUNK) {
+        const int cn = (half - c0) < PAIR_CHUNK ? (half - c0) : PAIR_CHUNK;
+        for (int k = tid; k < cn; k += nth) {
+          int p, qq;
+          circle_pair(rnd, c0 + k, np, p, qq);
+          Rot<R, E> rp;
+          rp.p = p; rp.q = -1; rp.c = 1; rp.s = 0; rp.e = unit_e<E>();
+          if (qq < n) {
+            const R a = re(A[(long long)p * n + p]), b = re(A[(long long)qq * n + qq]);
+            const E gpq = A[(long long)p * n + qq];
+            const R hh = absv(gpq);
+            if (hh > tol_rel * sqrt(fabs(a * b)) && hh > tol_abs) {
+              const R tau = (b - a) / (2 * hh);
+              const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+              rp.q = qq;
+              rp.c = (R)1 / sqrt((R)1 + tt * tt);
+              rp.s = tt * rp.c;
+              rp.e = divr<E, R>(gpq, hh);
+              flags[0] = 1;
+              atomicAdd(&flags[1], 1);
+            }
           }
+          rot[k] = rp;
         }
-        rot[k] = rp;
+        __syncthreads();
+        // columns: [x, y] <- [c x - s y conj(e), s x + c y conj(e)]
+        for (int w2 = tid; w2 < n * cn; w2 += nth) {
+          const int i = w2 / cn, k = w2 % cn;
+          const Rot<R, E> rp = rot[k];
+          if (rp.q < 0) continue;
+          const E ec = cj(rp.e);
+          E* Ai = A + (long long)i * n;
+          const E x = Ai[rp.p], ys = mulv(Ai[rp.q], ec);
+          Ai[rp.p] = lin(rp.c, x, -rp.s, ys);
+          Ai[rp.q] = lin(rp.s, x, rp.c, ys);
+          E* Vi = V + (long long)i * n;
+          const E vx = Vi[rp.p], vys = mulv(Vi[rp.q], ec);
+          Vi[rp.p] = lin(rp.c, vx, -rp.s, vys);
+          Vi[rp.q] = lin(rp.s, vx, rp.c, vys);
+        }
+        __syncthreads();
+        // rows: [x; y] <- [c x - s e y; s x + c e y]
+        for (int w2 = tid; w2 < n * cn; w2 += nth) {
+          const int k = w2 / n, i = w2 % n;
+          const Rot<R, E> rp = rot[k];
+          if (rp.q < 0) continue;
+          const E x = A[(long long)rp.p * n + i], ye = mulv(rp.e, A[(long long)rp.q * n + i]);
+          A[(long long)rp.p * n + i] = lin(rp.c, x, -rp.s, ye);
+          A[(long long)rp.q * n + i] = lin(rp.s, x, rp.c, ye);
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      // columns: [x, y] <- [c x - s y conj(e), s x + c y conj(e)]
-      for (int w2 = tid; w2 < n * half; w2 += nth) {
-        const int i = w2 / half, k = w2 % half;
-        const Rot<R, E> rp = rot[k];
-        if (rp.q < 0) continue;
-        const E ec = cj(rp.e);
-        E* Ai = A + (long long)i * n;
-        const E x = Ai[rp.p], ys = mulv(Ai[rp.q], ec);
-        Ai[rp.p] = lin(rp.c, x, -rp.s, ys);
-        Ai[rp.q] = lin(rp.s, x, rp.c, ys);
-        E* Vi = V + (long long)i * n;
-        const E vx = Vi[rp.p], vys = mulv(Vi[rp.q], ec);
-        Vi[rp.p] = lin(rp.c, vx, -rp.s, vys);
-        Vi[rp.q] = lin(rp.s, vx, rp.c, vys);
-      }
-      __syncthreads();
-      // rows: [x; y] <- [c x - s e y; s x + c e y]
-      for (int w2 = tid; w2 < n * half; w2 += nth) {
-        const int k = w2 / n, i = w2 % n;
-        const Rot<R, E> rp = rot[k];
-        if (rp.q < 0) continue;
-        const E x = A[(long long)rp.p * n + i], ye = mulv(rp.e, A[(long long)rp.q * n + i]);
-        A[(long long)rp.p * n + i] = lin(rp.c, x, -rp.s, ye);
-        A[(long long)rp.q * n + i] = lin(rp.s, x, rp.c, ye);
+    }
+    if (!flags[0]) break;
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// One-sided rotation parameters from the column 2x2 Gram [[al, ga], [conj ga, be]].
+// Returns false when the pair is already orthogonal to the path's tolerance or one
+// column is at or below the selection floor.  The FP64 path takes the angle from
+// FP32 arithmetic (its accuracy only sets the convergence rate) and makes c, s and
+// e exactly unitary in FP64 by Newton steps on FP32 reciprocal square roots, which
+// avoids FP64 division and square root (slow on this part).
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  double r = rsqrt(x);               // FP64 approximation, no division
+  return r * (1.5 - 0.5 * x * r * r);  // one Newton step to full precision
+}
+__device__ __forceinline__ bool os_params(double al, double be, double2 ga, bool selfm, double tol_abs,
+                                          double col_floor, double& c, double& s, double2& e) {
+  if (selfm) ga.y = 0;
+  const double g2 = ga.x * ga.x + ga.y * ga.y;
+  const double rel = Prec<double>::os_rel;
+  if (!(g2 > rel * rel * al * be && g2 > tol_abs * tol_abs && al > col_floor && be > col_floor)) return false;
+  const double inv = rsqrt_newton(g2);
+  const double tau = (be - al) * 0.5 * inv;
+  if (fabs(tau) > 1e30) return false;  // angle below any representable rotation
+  const float tf = (float)tau, af = fabsf(tf);
+  // t = sign / (|tau| + sqrt(1 + tau^2)); for |tau| > 1e4 this is 1 / (2 |tau|) to
+  // FP32 accuracy, and tau^2 would overflow FP32 beyond ~1.8e19
+  const float t32 = (tf >= 0.f ? 1.f : -1.f) * (af > 1e4f ? 0.5f / af : 1.f / (af + sqrtf(1.f + tf * tf)));
+  const double t = (double)t32;
+  c = rsqrt_newton(1.0 + t * t);
+  s = t * c;
+  e = make_double2(ga.x * inv, ga.y * inv);
+  return true;
+}
+__device__ __forceinline__ bool os_params(float al, float be, float2 ga, bool selfm, float tol_abs,
+                                          float col_floor, float& c, float& s, float2& e) {
+  if (selfm) ga.y = 0;
+  const float hh = hypotf(ga.x, ga.y);
+  if (!(hh > Prec<float>::os_rel * sqrtf(al * be) && hh > tol_abs && al > col_floor && be > col_floor)) return false;
+  const float tau = (be - al) / (2.f * hh);
+  const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  c = rsqrtf(1.f + t * t);
+  s = t * c;
+  e = make_float2(ga.x / hh, ga.y / hh);
+  return true;
+}
+
+template <typename R> struct PairWork {
+  R al, be, c, s;
+  typename Prec<R>::C ga, e;
+  int act;
+};
+
+// One-sided Jacobi sweeps on the n columns (length h) of W, the same rotations on the
+// columns (length n) of Vc.  Each round: inner products (one warp per pair), rotation
+// parameters (one thread per pair), updates (one warp per pair).
+// FP32: one phase per round -- each warp computes its pair's inner products, the
+// rotation (redundantly in every lane, cheap in FP32) and the update.
+__device__ int refine_sweeps_fp32(float2* W, float2* Vc, int n, int h, bool selfm, float tol_abs, float col_floor,
+                                  int* flags) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int np = n + (n & 1), half = np / 2;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    __syncthreads();
+    if (tid == 0) flags[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int k = warp; k < half; k += nwarp) {
+        int p, qq;
+        circle_pair(rnd, k, np, p, qq);
+        if (qq >= n) continue;
+        float2* wp = W + (long long)p * h;
+        float2* wq = W + (long long)qq * h;
+        float al = 0.f, be = 0.f;
+        float2 ga = make_float2(0.f, 0.f);
+        for (int x = lane; x < h; x += 32) {
+          const float2 a = wp[x], b = wq[x];
+          al += a.x * a.x + a.y * a.y;
+          be += b.x * b.x + b.y * b.y;
+          cfma_cj(ga, a, b);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+        }
+        float c, sn;
+        float2 e;
+        if (!os_params(al, be, ga, selfm, tol_abs, col_floor, c, sn, e)) continue;  // warp-uniform
+        const float2 ec = cj(e);
+        for (int x = lane; x < h; x += 32) {
+          const float2 a = wp[x], bs = mulv(wq[x], ec);
+          wp[x] = lin(c, a, -sn, bs);
+          wq[x] = lin(sn, a, c, bs);
+        }
+        float2* vp = Vc + (long long)p * n;
+        float2* vq = Vc + (long long)qq * n;
+        for (int x = lane; x < n; x += 32) {
+          const float2 a = vp[x], bs = mulv(vq[x], ec);
+          vp[x] = lin(c, a, -sn, bs);
+          vq[x] = lin(sn, a, c, bs);
+        }
+        if (lane == 0) { flags[0] = 1; atomicAdd(&flags[1], 1); }
       }
       __syncthreads();
     }
@@ -610,23 +728,84 @@ __device__ int jacobi(E* A, E* V, int n, Rot<R, E>* rot, int* flags, R tol_rel, 
   return sweep;
 }
 
-// Shared-memory layout of the eigensolver for blocks up to nmax: rotation list,
-// mirror positions, bond segments, flags, then A and V.
-struct EigLayout {
-  size_t rot, mpos, seg, flags, A, total_fixed;
-};
 template <typename R>
-__host__ __device__ inline EigLayout eig_layout(int nmax) {
+__device__ int refine_sweeps(typename Prec<R>::C* W, typename Prec<R>::C* Vc, int n, int h, bool selfm,
+                             R tol_abs, R col_floor, PairWork<R>* pw, int* flags) {
   typedef typename Prec<R>::C C;
-  EigLayout L;
-  size_t o = 0;
-  L.rot = o; o += (size_t)(nmax / 2 + 1) * sizeof(Rot<R, C>); o = (o + 15) & ~(size_t)15;
-  L.mpos = o; o += (size_t)nmax * sizeof(int); o = (o + 15) & ~(size_t)15;
-  L.seg = o; o += (size_t)(MPO_P_MAX + 2) * sizeof(int); o = (o + 15) & ~(size_t)15;
-  L.flags = o; o += 4 * sizeof(int); o = (o + 15) & ~(size_t)15;
-  L.A = o;
-  L.total_fixed = o;
-  return L;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int np = n + (n & 1), half = np / 2;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    __syncthreads();
+    if (tid == 0) flags[0] = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int c0 = 0; c0 < half; c0 += PAIR_CHUNK) {
+        const int cn = (half - c0) < PAIR_CHUNK ? (half - c0) : PAIR_CHUNK;
+        for (int k = warp; k < cn; k += nwarp) {
+          int p, qq;
+          circle_pair(rnd, c0 + k, np, p, qq);
+          if (qq >= n) { if (lane == 0) pw[k].act = 0; continue; }
+          const C* wp = W + (long long)p * h;
+          const C* wq = W + (long long)qq * h;
+          R al = 0, be = 0;
+          C ga = zero_e<C>();
+          for (int x = lane; x < h; x += 32) {
+            const C a = wp[x], b = wq[x];
+            al += a.x * a.x + a.y * a.y;
+            be += b.x * b.x + b.y * b.y;
+            cfma_cj(ga, a, b);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+            ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+          }
+          if (lane == 0) { pw[k].al = al; pw[k].be = be; pw[k].ga = ga; pw[k].act = 1; }
+        }
+        __syncthreads();
+        for (int k = tid; k < cn; k += nth) {
+          if (!pw[k].act) continue;
+          R c, s;
+          C e;
+          if (os_params(pw[k].al, pw[k].be, pw[k].ga, selfm, tol_abs, col_floor, c, s, e)) {
+            pw[k].c = c; pw[k].s = s; pw[k].e = e;
+            flags[0] = 1;
+            atomicAdd(&flags[1], 1);
+          } else {
+            pw[k].act = 0;
+          }
+        }
+        __syncthreads();
+        for (int k = warp; k < cn; k += nwarp) {
+          if (!pw[k].act) continue;
+          int p, qq;
+          circle_pair(rnd, c0 + k, np, p, qq);
+          const R cs = pw[k].c, sn = pw[k].s;
+          const C ec = cj(pw[k].e);
+          C* wp = W + (long long)p * h;
+          C* wq = W + (long long)qq * h;
+          for (int x = lane; x < h; x += 32) {
+            const C a = wp[x], bs = mulv(wq[x], ec);
+            wp[x] = lin(cs, a, -sn, bs);
+            wq[x] = lin(sn, a, cs, bs);
+          }
+          C* vp = Vc + (long long)p * n;
+          C* vq = Vc + (long long)qq * n;
+          for (int x = lane; x < n; x += 32) {
+            const C a = vp[x], bs = mulv(vq[x], ec);
+            vp[x] = lin(cs, a, -sn, bs);
+            vq[x] = lin(sn, a, cs, bs);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (!flags[0]) break;
+  }
+  __syncthreads();
+  return sweep;
 }
 
 __device__ __forceinline__ int mirror_coord(const Slot& sl, const MpoDev& st, const GateDesc& g, int t,
@@ -645,40 +824,54 @@ __device__ __forceinline__ int mirror_coord(const Slot& sl, const MpoDev& st, co
   return off + pos;
 }
 
-// ---------------------------------------------------------------- k_eig
-// One CTA per canonical block of size class SMALL (n <= SMALL_N) or large (n > SMALL_N).
-template <typename R, bool SMALL>
-__global__ void __launch_bounds__(SMALL ? 128 : 256) k_eig(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
-                                                          int nmax, int smem_bytes) {
-  typedef typename Prec<R>::C C;
-  const int t = blockIdx.x, s = blockIdx.y;
-  Slot sl = get_slot(ws, s);
-  if (sl.scal[SS_STATUS] || t >= ws.Pc) return;
-  const int n = sl.f(BF_G, t);
-  if (n == 0 || (SMALL ? n > SMALL_N : n <= SMALL_N)) return;
-  const GateDesc g = gates[s];
-  const int side = sl.f(BF_SIDE, t), m = sl.f(BF_M, t);
+// Shared-memory layout of k_svd (host and device agree through this function).
+struct SvdLayout {
+  size_t hdr, pw, mpos, seg, nrm, data, total;
+};
+template <typename R>
+__host__ __device__ inline SvdLayout svd_layout(int D, size_t total) {
+  SvdLayout L;
+  size_t o = 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  L.hdr = o; o = al(o + 64);
+  const size_t pwb = (size_t)PAIR_CHUNK * sizeof(PairWork<R>);
+  const size_t rtb = (size_t)PAIR_CHUNK * sizeof(Rot<float, float2>);
+  L.pw = o; o = al(o + (pwb > rtb ? pwb : rtb));
+  L.mpos = o; o = al(o + (size_t)D * sizeof(int));
+  L.seg = o; o = al(o + (size_t)(MPO_P_MAX + 2) * sizeof(int));
+  L.nrm = o; o = al(o + (size_t)(D > 32 ? D : 32) * sizeof(R));
+  L.data = o;
+  L.total = total;
+  return L;
+}
+
+// FP32 seed for one canonical block: Gram eigenvectors by two-sided Jacobi (real
+// arithmetic in the mirror-conjugation basis for self-mirror blocks), written
+// row-major to the slot's V buffer as complex FP32.
+__device__ void seed_block(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, unsigned char* smem,
+                           const SvdLayout& L) {
+  typedef float R;
+  typedef float2 C;
+  const int n = sl.f(BF_G, t), side = sl.f(BF_SIDE, t), m = sl.f(BF_M, t);
   const int ncap = st.ncap, P = st.P, M = st.M;
   const bool selfm = pair_mirror(m, ncap) == m;
   const int tid = threadIdx.x, nth = blockDim.x;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const EigLayout L = eig_layout<R>(nmax);
+  int* flags = reinterpret_cast<int*>(smem + L.hdr);
   int* mpos = reinterpret_cast<int*>(smem + L.mpos);
   int* segX = reinterpret_cast<int*>(smem + L.seg);
-  int* flags = reinterpret_cast<int*>(smem + L.flags);
+  const size_t room = L.total - L.data;
   C* gG = reinterpret_cast<C*>(sl.G) + sl.f(BF_GOFF, t);
   C* gV = reinterpret_cast<C*>(sl.V) + sl.f(BF_GOFF, t);
-  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
-  int sweeps;
+  if (tid == 0) { flags[0] = 0; flags[1] = 0; }  // published by the barriers below
   if (selfm) {
-    const bool in_smem = L.total_fixed + 2ull * n * n * sizeof(R) <= (size_t)smem_bytes;
+    const bool in_smem = 2ull * n * n * sizeof(R) <= room;
     const long long bX = (long long)g.inst * (M + 1) + g.j + (side == 0 ? 0 : 2);
     for (int p = tid; p <= P; p += nth) segX[p] = st.segoff[bX * (P + 1) + p];
     __syncthreads();
     for (int i = tid; i < n; i += nth) mpos[i] = mirror_coord(sl, st, g, t, side, i, segX);
     __syncthreads();
     // real Gram in the basis e_i (fixed), (e_p + e_q)/sqrt2 at p, i(e_p - e_q)/sqrt2 at q (p < q)
-    R* A = in_smem ? reinterpret_cast<R*>(smem + L.A) : reinterpret_cast<R*>(gV);
+    R* A = in_smem ? reinterpret_cast<R*>(smem + L.data) : reinterpret_cast<R*>(gV);
     R* V = in_smem ? A + (long long)n * n : reinterpret_cast<R*>(gG);
     const R h = (R)0.70710678118654752440;
     for (int e = tid; e < n * n; e += nth) {
@@ -697,22 +890,8 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256) k_eig(MpoDev st, SlotWS ws,
       A[(long long)i * n + j] = acc;
     }
     __syncthreads();  // gG fully read before V (global mode) overwrites it
-    sweeps = jacobi<R, R>(A, V, n, reinterpret_cast<Rot<R, R>*>(smem + L.rot), flags, Prec<R>::tol_rel,
-                          Prec<R>::tol_abs);
-    // eigenvalues first (A's storage is reused below in global mode)
-    const int coff = sl.f(BF_COFF, t);
-    for (int i = tid; i < n; i += nth) {
-      const R wi = A[(long long)i * n + i];
-      int rank = 0;
-      for (int j = 0; j < n; ++j) {
-        const R wj = A[(long long)j * n + j];
-        rank += (wj > wi) || (wj == wi && j < i);
-      }
-      if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4000 + t);
-      sl.sval[coff + rank] = sqrt(fmax((double)wi, 0.0));
-      sl.perm[coff + rank] = i;
-    }
-    __syncthreads();
+    const int sweeps = jacobi<R, R>(A, V, n, reinterpret_cast<Rot<R, R>*>(smem + L.pw), flags,
+                                    Prec<R>::tol_rel, Prec<R>::tol_abs);
     // eigenvectors back to the original basis: x = W x~ (x~ real).  In global mode A
     // (dead now) shares gV's storage and V lives in gG, so writing gV is safe.
     for (int e = tid; e < n * n; e += nth) {
@@ -730,41 +909,239 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256) k_eig(MpoDev st, SlotWS ws,
       atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
       atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
     }
-    if (sweeps >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3000 + t);
-    return;
-  }
-  // complex Hermitian block
-  const bool in_smem = L.total_fixed + 2ull * n * n * sizeof(C) <= (size_t)smem_bytes;
-  C* A = in_smem ? reinterpret_cast<C*>(smem + L.A) : gG;
-  C* V = in_smem ? A + (long long)n * n : gV;
-  if (in_smem) {
-    for (int e = tid; e < n * n; e += nth) A[e] = gG[e];
+  } else {
+    const bool in_smem = 2ull * n * n * sizeof(C) <= room;
+    C* A = in_smem ? reinterpret_cast<C*>(smem + L.data) : gG;
+    C* V = in_smem ? A + (long long)n * n : gV;
+    if (in_smem) {
+      for (int e = tid; e < n * n; e += nth) A[e] = gG[e];
+    }
+    __syncthreads();
+    const int sweeps = jacobi<R, C>(A, V, n, reinterpret_cast<Rot<R, C>*>(smem + L.pw), flags,
+                                    Prec<R>::tol_rel, Prec<R>::tol_abs);
+    if (in_smem) {
+      for (int e = tid; e < n * n; e += nth) gV[e] = V[e];
+    }
+    if (st.ctr && tid == 0) {
+      // per active rotation and per index: A columns, A rows and V columns, 18 flops each
+      atomicAdd(st.ctr + CTR_EIG, 54ull * (unsigned long long)n * (unsigned long long)flags[1]);
+      atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
+      atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+    }
   }
   __syncthreads();
-  sweeps = jacobi<R, C>(A, V, n, reinterpret_cast<Rot<R, C>*>(smem + L.rot), flags, Prec<R>::tol_rel,
-                        Prec<R>::tol_abs);
+}
+
+// ---------------------------------------------------------------- refinement
+// One-sided Jacobi (Hestenes) refinement of each canonical block's SVD.  The Gram
+// eigenvectors V (n x n, FP32 seed) give W = Theta V (side 1, n = cols) or
+// W = Theta^dag V (side 0, n = rows), whose n columns are orthogonal up to the seed's
+// error.  Sweeps of pairwise rotations that orthogonalise the columns of W (the 2x2
+// Gram [[|w_p|^2, w_p^dag w_q], [., |w_q|^2]] recomputed from W at each step, the same
+// rotation applied to V) converge quadratically to the SVD of Theta without squaring
+// its condition number: s_k = |w_k|.  Both factors come out: side 1:
+// X[:, k] = w_k / s_k, Y[k, :] = conj(v_k);  side 0: X[:, k] = v_k,
+// Y[k, :] = conj(w_k) / s_k.  W (h x n) and V (n x n) are column-major, in shared
+// memory when they fit, else in the slot scratch (W buffer, VC buffer).  For
+// self-mirror blocks the columns are mirror-symmetric, so w_p^dag w_q is real in exact
+// arithmetic; its imaginary part (rounding) is dropped to keep the rotations real.
+template <typename R>
+__device__ void refine_block(const MpoDev& st, const Slot& sl, int t, unsigned char* smem, const SvdLayout& L,
+                             bool seeded) {
+  typedef typename Prec<R>::C C;
+  const int n = sl.f(BF_G, t);
+  const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
+  const int h = side == 0 ? c : r;
+  const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  int* flags = reinterpret_cast<int*>(smem + L.hdr);
+  R* nrm = reinterpret_cast<R*>(smem + L.nrm);
+  PairWork<R>* pw = reinterpret_cast<PairWork<R>*>(smem + L.pw);
+  const size_t room = L.total - L.data;
+  const bool w_smem = (size_t)h * n * sizeof(C) <= room;
+  const bool in_smem = ((size_t)h * n + (size_t)n * n) * sizeof(C) <= room;  // V too
+  const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
+  const float2* V0 = reinterpret_cast<const float2*>(sl.V) + sl.f(BF_GOFF, t);  // row-major FP32 seed
+  C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);
+  C* gVc = reinterpret_cast<C*>(sl.VC) + sl.f(BF_GOFF, t);
+  C* W = w_smem ? reinterpret_cast<C*>(smem + L.data) : gW;
+  C* Vc = in_smem ? W + (size_t)h * n : gVc;
+  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
+  if (!seeded) {
+    // no seed (the Gram eigensolver did not fit): plain one-sided Jacobi from V = I
+    for (int e = tid; e < n * n; e += nth) Vc[e] = ((e / n) == (e % n)) ? unit_e<C>() : zero_e<C>();
+  } else if (sizeof(R) == 8) {
+    // The FP32 seed is unitary only to ~1e-7 and the rotations below keep any
+    // non-unitarity, so it is first orthonormalised in FP64 by two Newton-Schulz
+    // steps V <- V (3 I - V^dag V) / 2 (error delta -> ~delta^2 per step), in global
+    // scratch: S = V^dag V in the slot's NS buffer, V S in the W buffer (free until W
+    // is formed below).
+    C* S = reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t);
+    C* T = gW;
+    for (int e = tid; e < n * n; e += nth) T[e] = cvt<C>(to_d2(V0[(long long)(e % n) * n + e / n]));
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      for (int e = tid; e < n * n; e += nth) {  // S[a][b] = v_a^dag v_b (column-major)
+        const int b = e / n, a = e % n;
+        C acc = zero_e<C>();
+        for (int i = 0; i < n; ++i) cfma_cj(acc, gVc[(long long)a * n + i], gVc[(long long)b * n + i]);
+        S[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) {  // T[:, b] = sum_a V[:, a] (3 delta_ab - S_ab) / 2
+        const int b = e / n, i = e % n;
+        C acc = zero_e<C>();
+        for (int a = 0; a < n; ++a) {
+          C w = S[(long long)b * n + a];
+          w.x = (a == b ? (R)1.5 : (R)0) - (R)0.5 * w.x;
+          w.y = -(R)0.5 * w.y;
+          cfma(acc, gVc[(long long)a * n + i], w);
+        }
+        T[e] = acc;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
+      __syncthreads();
+    }
+    if (in_smem) {
+      for (int e = tid; e < n * n; e += nth) Vc[e] = gVc[e];
+    }
+  } else {
+    for (int e = tid; e < n * n; e += nth) {  // column-major copy of V
+      const int k = e / n, i = e % n;
+      Vc[e] = cvt<C>(to_d2(V0[(long long)i * n + k]));
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < h * n; e += nth) {
+    const int k = e / h, x = e % h;
+    C acc = zero_e<C>();
+    if (side == 1) {
+      for (int q = 0; q < n; ++q) cfma(acc, Th[(long long)x * c + q], Vc[(long long)k * n + q]);
+    } else {
+      for (int i = 0; i < n; ++i) cfma_cj(acc, Th[(long long)i * c + x], Vc[(long long)k * n + i]);
+    }
+    W[e] = acc;
+  }
+  __syncthreads();
+  // largest column norm^2 (scale of the absolute thresholds)
+  R mx = 0;
+  for (int k = warp; k < n; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    mx = fmax(mx, a);
+  }
+  if (lane == 0) nrm[warp] = mx;
+  __syncthreads();
+  mx = 0;
+  for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
+  __syncthreads();
+  // columns at or below the selection floor are dropped anyway: rotating them only
+  // churns rounding noise, so pairs involving one are skipped
+  int sweeps;
+  if (sizeof(R) == 8)
+    sweeps = refine_sweeps<R>(W, Vc, n, h, selfm, Prec<R>::os_abs * mx, (R)Prec<R>::floor * mx, pw, flags);
+  else
+    sweeps = refine_sweeps_fp32(reinterpret_cast<float2*>(W), reinterpret_cast<float2*>(Vc), n, h, selfm,
+                                (float)(Prec<R>::os_abs * mx), (float)(Prec<R>::floor * mx), flags);
+  if (sweeps >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
+  // singular values = column norms, ranked descending (ties by index)
+  for (int k = warp; k < n; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) nrm[k] = a;
+  }
+  __syncthreads();
   const int coff = sl.f(BF_COFF, t);
   for (int i = tid; i < n; i += nth) {
-    const R wi = A[(long long)i * n + i].x;
+    const R wi = nrm[i];
     int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const R wj = A[(long long)j * n + j].x;
-      rank += (wj > wi) || (wj == wi && j < i);
-    }
-    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4000 + t);
-    sl.sval[coff + rank] = sqrt(fmax((double)wi, 0.0));
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4500 + t);
+    sl.sval[coff + rank] = sqrt((double)wi);
     sl.perm[coff + rank] = i;
   }
+  if (w_smem) {
+    for (int e = tid; e < h * n; e += nth) gW[e] = W[e];
+  }
   if (in_smem) {
-    for (int e = tid; e < n * n; e += nth) gV[e] = V[e];
+    for (int e = tid; e < n * n; e += nth) gVc[e] = Vc[e];
   }
   if (st.ctr && tid == 0) {
-    // per active rotation and per index: A columns, A rows and V columns, 18 flops each
-    atomicAdd(st.ctr + CTR_EIG, 54ull * (unsigned long long)n * (unsigned long long)flags[1]);
-    atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
-    atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+    // per applied rotation: 3 inner products (24 h) and 2 x 12 (h + n) for the updates
+    atomicAdd(st.ctr + CTR_REFINE, (unsigned long long)flags[1] * (48ull * h + 24ull * n) +
+                                       8ull * (unsigned long long)h * n * n);
+    atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sweeps + 1));
   }
-  if (sweeps >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3000 + t);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- k_order, k_svd
+// The blocks of all gates of a layer go into one list, longest first (bucketed by
+// log2 of an n^2 (n + h) work estimate), for k_svd's persistent CTAs to take in that
+// order (longest-processing-time scheduling): small blocks fill the SMs around the
+// few large ones instead of holding an SM each.  The order inside a bucket does not
+// matter: every block's factorisation depends on its own data only.
+__global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter) {
+  __shared__ int hist[64], start[64];
+  const int tid = threadIdx.x, Pc = ws.Pc, E = ngates * Pc;
+  if (tid < 64) hist[tid] = 0;
+  __syncthreads();
+  for (int e = tid; e < E; e += blockDim.x) {
+    Slot sl = get_slot(ws, e / Pc);
+    const int t = e % Pc;
+    if (sl.scal[SS_STATUS] || sl.f(BF_G, t) == 0) continue;
+    const double n = sl.f(BF_G, t), h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
+    const int key = 63 - min(63, (int)log2(n * n * (n + h) + 1.0));
+    atomicAdd(&hist[key], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int k = 0; k < 64; ++k) { start[k] = acc; acc += hist[k]; }
+    counter[0] = 0;
+    counter[1] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < E; e += blockDim.x) {
+    Slot sl = get_slot(ws, e / Pc);
+    const int t = e % Pc;
+    if (sl.scal[SS_STATUS] || sl.f(BF_G, t) == 0) continue;
+    const double n = sl.f(BF_G, t), h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
+    const int key = 63 - min(63, (int)log2(n * n * (n + h) + 1.0));
+    list[atomicAdd(&start[key], 1)] = e;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
+                                             const int* __restrict__ list, int* counter, int smem_bytes) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  const SvdLayout L = svd_layout<R>(ws.D, (size_t)smem_bytes);
+  int* hdr = reinterpret_cast<int*>(smem + L.hdr);
+  const int total = counter[1];
+  for (;;) {
+    if (threadIdx.x == 0) hdr[8] = atomicAdd(&counter[0], 1);
+    __syncthreads();
+    const int idx = hdr[8];
+    __syncthreads();
+    if (idx >= total) break;
+    const int e = list[idx];
+    const int s = e / ws.Pc, t = e % ws.Pc;
+    Slot sl = get_slot(ws, s);
+    const GateDesc g = gates[s];
+    // the FP32 Gram seed runs only when its matrices fit in shared memory; a seed in
+    // global memory costs more than the extra one-sided sweeps it would save
+    const int n = sl.f(BF_G, t);
+    const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
+    const bool seeded = 2ull * n * n * (selfm ? sizeof(float) : sizeof(float2)) <= L.total - L.data;
+    if (seeded) seed_block(st, sl, g, t, smem, L);
+    refine_block<R>(st, sl, t, smem, L, seeded);
+  }
 }
 
 // ---------------------------------------------------------------- k_select
@@ -956,204 +1333,6 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
 }
 
 
-// ---------------------------------------------------------------- k_refine
-// One-sided Jacobi (Hestenes) refinement of each canonical block's SVD.  The Gram
-// eigenvectors V (n x n, from k_eig) give W = Theta V (side 1, n = cols) or
-// W = Theta^dag V (side 0, n = rows), whose n columns are orthogonal up to the Gram
-// eigensolver's error.  Sweeps of pairwise rotations that orthogonalise the columns
-// of W (the 2x2 Gram [[|w_p|^2, w_p^dag w_q], [., |w_q|^2]] recomputed from W at each
-// step, the same rotation applied to V) converge quadratically to the SVD of Theta
-// without squaring its condition number: s_k = |w_k|.  Both factors come out:
-// side 1: X[:, k] = w_k / s_k, Y[k, :] = conj(v_k);  side 0: X[:, k] = v_k,
-// Y[k, :] = conj(w_k) / s_k.  W (h x n) and V (n x n) are column-major, in shared
-// memory when they fit, else in the slot scratch (W buffer, G buffer).
-template <typename R>
-__global__ void __launch_bounds__(256) k_refine(MpoDev st, SlotWS ws, int smem_bytes) {
-  typedef typename Prec<R>::C C;
-  const int t = blockIdx.x, s = blockIdx.y;
-  Slot sl = get_slot(ws, s);
-  if (sl.scal[SS_STATUS] || t >= ws.Pc) return;
-  const int n = sl.f(BF_G, t);
-  if (n == 0) return;
-  const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
-  const int h = side == 0 ? c : r;
-  const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  extern __shared__ __align__(16) unsigned char smem[];
-  int* flags = reinterpret_cast<int*>(smem);
-  R* nrm = reinterpret_cast<R*>(smem + 16);  // [max(n, 32)]: column norms, also per-warp scratch
-  const int nn = n > 32 ? n : 32;
-  size_t off = 16 + (((size_t)nn * sizeof(R) + 15) & ~(size_t)15);
-  const bool in_smem = off + ((size_t)h * n + (size_t)n * n) * sizeof(C) <= (size_t)smem_bytes;
-  const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
-  const float2* V0 = reinterpret_cast<const float2*>(sl.V) + sl.f(BF_GOFF, t);  // row-major FP32 seed
-  C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);
-  C* gVc = reinterpret_cast<C*>(sl.G) + sl.f(BF_GOFF, t);             // the Gram is dead now
-  C* W = in_smem ? reinterpret_cast<C*>(smem + off) : gW;
-  C* Vc = in_smem ? W + (size_t)h * n : gVc;
-  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
-  if (sizeof(R) == 8) {
-    // The FP32 seed is unitary only to ~1e-7 and the rotations below keep any
-    // non-unitarity, so it is first orthonormalised in FP64 by two Newton-Schulz
-    // steps V <- V (3 I - V^dag V) / 2 (error delta -> ~delta^2 per step), in global
-    // scratch: S = V^dag V in the slot's NS buffer, V S in the W buffer (free until W
-    // is formed below).
-    C* S = reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t);
-    C* T = gW;
-    for (int e = tid; e < n * n; e += nth) T[e] = cvt<C>(to_d2(V0[(long long)(e % n) * n + e / n]));
-    __syncthreads();
-    for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
-    __syncthreads();
-    for (int it = 0; it < 2; ++it) {
-      for (int e = tid; e < n * n; e += nth) {  // S[a][b] = v_a^dag v_b (column-major)
-        const int b = e / n, a = e % n;
-        C acc = zero_e<C>();
-        for (int i = 0; i < n; ++i) cfma_cj(acc, gVc[(long long)a * n + i], gVc[(long long)b * n + i]);
-        S[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < n * n; e += nth) {  // T[:, b] = sum_a V[:, a] (3 delta_ab - S_ab) / 2
-        const int b = e / n, i = e % n;
-        C acc = zero_e<C>();
-        for (int a = 0; a < n; ++a) {
-          C w = S[(long long)b * n + a];
-          w.x = (a == b ? (R)1.5 : (R)0) - (R)0.5 * w.x;
-          w.y = -(R)0.5 * w.y;
-          cfma(acc, gVc[(long long)a * n + i], w);
-        }
-        T[e] = acc;
-      }
-      __syncthreads();
-      for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
-      __syncthreads();
-    }
-    if (in_smem) {
-      for (int e = tid; e < n * n; e += nth) Vc[e] = gVc[e];
-    }
-  } else {
-    for (int e = tid; e < n * n; e += nth) {  // column-major copy of V
-      const int k = e / n, i = e % n;
-      Vc[e] = cvt<C>(to_d2(V0[(long long)i * n + k]));
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < h * n; e += nth) {
-    const int k = e / h, x = e % h;
-    C acc = zero_e<C>();
-    if (side == 1) {
-      for (int q = 0; q < n; ++q) cfma(acc, Th[(long long)x * c + q], Vc[(long long)k * n + q]);
-    } else {
-      for (int i = 0; i < n; ++i) cfma_cj(acc, Th[(long long)i * c + x], Vc[(long long)k * n + i]);
-    }
-    W[e] = acc;
-  }
-  __syncthreads();
-  // largest column norm^2 (scale of the absolute threshold)
-  R mx = 0;
-  for (int k = warp; k < n; k += nwarp) {
-    R a = 0;
-    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    mx = fmax(mx, a);
-  }
-  if (lane == 0) nrm[warp] = mx;
-  __syncthreads();
-  mx = 0;
-  for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
-  __syncthreads();
-  const R tol_abs = Prec<R>::os_abs * mx;
-  // columns at or below the selection floor are dropped anyway: rotating them only
-  // churns rounding noise, so pairs involving one are skipped
-  const R col_floor = (R)Prec<R>::floor * mx;
-  const int np = n + (n & 1), half = np / 2;
-  int sweep = 0;
-  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
-    if (tid == 0) flags[0] = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int k = warp; k < half; k += nwarp) {
-        int p, qq;
-        if (k == 0) { p = rnd; qq = np - 1; }
-        else { p = (rnd + k) % (np - 1); qq = (rnd - k + np - 1) % (np - 1); }
-        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
-        if (qq >= n) continue;
-        C* wp = W + (long long)p * h;
-        C* wq = W + (long long)qq * h;
-        R al = 0, be = 0;
-        C ga = zero_e<C>();
-        for (int x = lane; x < h; x += 32) {
-          const C a = wp[x], b = wq[x];
-          al += a.x * a.x + a.y * a.y;
-          be += b.x * b.x + b.y * b.y;
-          cfma_cj(ga, a, b);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
-          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
-        }
-        // self-mirror block: the columns are mirror-symmetric, so w_p^dag w_q is real
-        // in exact arithmetic; its imaginary part is rounding noise and a rotation with
-        // that phase would break the symmetry, so the rotation is kept real
-        if (selfm) ga.y = 0;
-        const R hh = absv(ga);
-        if (!(hh > Prec<R>::os_rel * sqrt(al * be) && hh > tol_abs && al > col_floor && be > col_floor))
-          continue;  // warp-uniform
-        const R tau = (be - al) / (2 * hh);
-        const R tt = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
-        const R cs = (R)1 / sqrt((R)1 + tt * tt), sn = tt * cs;
-        const C ec = cj(divr<C, R>(ga, hh));
-        for (int x = lane; x < h; x += 32) {
-          const C a = wp[x], bs = mulv(wq[x], ec);
-          wp[x] = lin(cs, a, -sn, bs);
-          wq[x] = lin(sn, a, cs, bs);
-        }
-        C* vp = Vc + (long long)p * n;
-        C* vq = Vc + (long long)qq * n;
-        for (int x = lane; x < n; x += 32) {
-          const C a = vp[x], bs = mulv(vq[x], ec);
-          vp[x] = lin(cs, a, -sn, bs);
-          vq[x] = lin(sn, a, cs, bs);
-        }
-        if (lane == 0) { flags[0] = 1; atomicAdd(&flags[1], 1); }
-      }
-      __syncthreads();
-    }
-    const int any = flags[0];
-    __syncthreads();
-    if (!any) break;
-  }
-  if (sweep >= JACOBI_MAX_SWEEPS && sizeof(R) == 8 && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
-  // singular values = column norms, ranked descending (ties by index)
-  for (int k = warp; k < n; k += nwarp) {
-    R a = 0;
-    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) nrm[k] = a;
-  }
-  __syncthreads();
-  const int coff = sl.f(BF_COFF, t);
-  for (int i = tid; i < n; i += nth) {
-    const R wi = nrm[i];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
-    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4500 + t);
-    sl.sval[coff + rank] = sqrt((double)wi);
-    sl.perm[coff + rank] = i;
-  }
-  if (in_smem) {
-    for (int e = tid; e < h * n; e += nth) gW[e] = W[e];
-    for (int e = tid; e < n * n; e += nth) gVc[e] = Vc[e];
-  }
-  if (st.ctr && tid == 0) {
-    // per applied rotation: 3 inner products (24 h) and 2 x 12 (h + n) for the updates
-    atomicAdd(st.ctr + CTR_REFINE, (unsigned long long)flags[1] * (48ull * h + 24ull * n) +
-                                       8ull * (unsigned long long)h * n * n);
-    atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sweep + 1));
-  }
-}
-
 // mirror of bond index a (segment of pair pa at position a - seg[pa]); -1 if the
 // mirror segment is too short (broken symmetry: reported, never dereferenced)
 __device__ __forceinline__ int mirror_index(const int* seg, const int* ch, int a, int ncap, int* err) {
@@ -1203,7 +1382,7 @@ __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const Gat
     const double isig = 1.0 / sl.sval[coff + k];
     const int vc = sl.perm[coff + k];
     const C* wk = reinterpret_cast<const C*>(sl.W) + sl.f(BF_TOFF, t) + (long long)vc * h;
-    const C* vk = reinterpret_cast<const C*>(sl.G) + sl.f(BF_GOFF, t) + (long long)vc * n;
+    const C* vk = reinterpret_cast<const C*>(sl.VC) + sl.f(BF_GOFF, t) + (long long)vc * n;
     const int* rmap = sl.rowmap + sl.f(BF_RMOFF, t);
     const int* cmap = sl.colmap + sl.f(BF_CMOFF, t);
     const int beta = sl.f(BF_NEWPOS, t) + k, betam = sl.f(BF_NEWPOS_MIR, t) + k;
@@ -1262,22 +1441,7 @@ int sm_count() {
   return g_sm_count;
 }
 
-constexpr size_t LARGE_SMEM_CAP = 200 * 1024;
-constexpr size_t REFINE_SMEM = 200 * 1024;
-
-template <typename R>
-size_t eig_smem_large(int D) {
-  typedef typename Prec<R>::C C;
-  const EigLayout L = eig_layout<R>(D);
-  const size_t full = L.total_fixed + 2ull * D * D * sizeof(C);
-  return full < LARGE_SMEM_CAP ? full : LARGE_SMEM_CAP;
-}
-template <typename R>
-size_t eig_smem_small() {
-  typedef typename Prec<R>::C C;
-  const EigLayout L = eig_layout<R>(SMALL_N);
-  return L.total_fixed + 2ull * SMALL_N * SMALL_N * sizeof(C);
-}
+constexpr size_t SVD_SMEM = 200 * 1024;
 
 template <typename R>
 void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
@@ -1286,8 +1450,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   int per = (4 * sms + ngates - 1) / ngates;
   if (per < 1) per = 1;
   if (per > 4096) per = 4096;
-  const size_t sm_small = eig_smem_small<float>();
-  const size_t sm_large = eig_smem_large<float>(ws.D);
+  const int nblk = ngates * ws.Pc;
+  const int nsvd = nblk < sms ? nblk : sms;
   if (ev) cudaEventRecord(ev[0], st);
   k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates);
   if (ev) cudaEventRecord(ev[1], st);
@@ -1295,11 +1459,9 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) cudaEventRecord(ev[2], st);
   k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
   if (ev) cudaEventRecord(ev[3], st);
-  k_eig<float, true><<<dim3(ws.Pc, ngates), 128, sm_small, st>>>(s, ws, d_gates, SMALL_N, (int)sm_small);
-  if (ws.D > SMALL_N)
-    k_eig<float, false><<<dim3(ws.Pc, ngates), 256, sm_large, st>>>(s, ws, d_gates, ws.D, (int)sm_large);
+  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter);
   if (ev) cudaEventRecord(ev[4], st);
-  k_refine<R><<<dim3(ws.Pc, ngates), 256, REFINE_SMEM, st>>>(s, ws, (int)REFINE_SMEM);
+  k_svd<R><<<nsvd, 256, SVD_SMEM, st>>>(s, ws, d_gates, ws.list, ws.counter, (int)SVD_SMEM);
   if (ev) cudaEventRecord(ev[5], st);
   k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
   if (ev) cudaEventRecord(ev[6], st);
@@ -1312,25 +1474,19 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
 // One-time per-process setup (called outside any stream capture).
 cudaError_t gate_module_init() {
   sm_count();
-  cudaError_t e = cudaFuncSetAttribute(k_eig<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)LARGE_SMEM_CAP);
+  cudaError_t e = cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_eig<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)eig_smem_small<float>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_refine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)REFINE_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_refine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)REFINE_SMEM);
+    e = cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
   return e;
 }
 
 // stage_events (optional, 8 events): recorded before each stage launch and after the
-// last one, for per-stage timing (setup, theta, gram, eig, refine, select, resplit).
+// last one, for per-stage timing (setup, theta, gram, order, svd, select, resplit).
 void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
                   int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
   if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev);
   else launch_layer_t<float>(s, ws, d_gates, ngates, d_disc, st, ev);
-  if (nlaunch) *nlaunch += ws.D > SMALL_N ? 8 : 7;
+  if (nlaunch) *nlaunch += 7;
 }
 
 void launch_phases(const MpoDev& s, const double* d_phase, cudaStream_t st) {

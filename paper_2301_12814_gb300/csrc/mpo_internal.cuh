@@ -101,6 +101,10 @@ struct SlotWS {
   int* items;      // [S][P*P] contraction items a*P + b
   double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
   double2* NS;     // [S][capGram] Newton-Schulz scratch V^dag V of the FP64 refinement
+  double2* VC;     // [S][capGram] refined right/left factors, column-major, path precision
+                   // (never aliases the FP32 Gram or seed buffers of other blocks)
+  int* list;       // [S * Pc] layer's blocks, longest first (k_order)
+  int* counter;    // [2]: next list entry, list length
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }

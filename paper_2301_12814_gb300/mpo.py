@@ -125,16 +125,17 @@ class Plan:
         _check(_lib().mpo_plan_discarded(self._h, _d(out)), "mpo_plan_discarded")
         return out[:self.n_total]
 
-    STAGES = ("setup", "theta", "gram", "eig", "refine", "select", "resplit", "phases")
+    STAGES = ("setup", "theta", "gram", "order", "svd", "select", "resplit", "phases")
 
     def profile(self, with_jacobi: bool = False):
         """One instrumented replay: {stage: (ms, launches, flops)} (and, if asked,
         {blocks, two-sided sweeps, one-sided sweeps})."""
-        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(3)
+        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(5)
         _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl), _d(jb)), "mpo_plan_profile")
         out = {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
         if with_jacobi:
-            return out, {"blocks": int(jb[0]), "sweeps": int(jb[1]), "refine_sweeps": int(jb[2])}
+            return out, {"blocks": int(jb[0]), "sweeps": int(jb[1]), "refine_sweeps": int(jb[2]),
+                         "seed_flops": float(jb[3]), "refine_flops": float(jb[4])}
         return out
 
     def close(self) -> None:
