@@ -126,6 +126,18 @@ def workload_arrays(wl, rank: int):
     return wl, meshes
 
 
+def aggregate_value(units: int, ms: float, ws: int, device) -> float:
+    """Whole-job updates/s: every rank processed `units` updates; the job took the
+    slowest rank's `ms` (max over ranks)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ws * units / (ms / 1e3)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -147,6 +159,46 @@ def run_reference(args, ws, rank):
         "e2e": {"value": val, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def observable_errors(a, b) -> dict:
+    """Largest error of run a against run b per observable: <n>, <n^2> relative,
+    S (bits) and Tr absolute, per-gate discarded weight relative to the largest."""
+    tr_a, n1_a, n2_a, S_a, d_a = a
+    tr_b, n1_b, n2_b, S_b, d_b = b
+    rel = lambda x, y: float(np.max(np.abs(x - y) / np.maximum(np.abs(y), 1e-300)))
+    return {"n_rel": rel(n1_a, n1_b), "n2_rel": rel(n2_a, n2_b), "S_abs": float(np.max(np.abs(S_a - S_b))),
+            "tr_abs": float(np.max(np.abs(tr_a - tr_b))),
+            "eps_rel": float(np.max(np.abs(d_a - d_b)) / max(float(np.max(np.abs(d_b))), 1e-300))}
+
+
+def compare_precision(args, wl, meshes, prec, n_gates, k, th, ph, fp, obs, stream):
+    """The same workload on the other path (mixed <-> FP64): its updates/s (graph
+    replays timed with CUDA events, a few steps) and the observable errors of the
+    mixed run against the FP64 run."""
+    import torch
+    import paper_2301_12814_gb300 as lib
+    other = "mixed_tf32" if prec == "fp64" else "fp64"
+    G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=other, stream=stream)
+    plan = G.plan_mesh(n_gates, k, th, ph, fp)
+    G.reset(); plan.run()
+    steps = max(1, min(args.steps, 5))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(steps):
+        G.reset()
+        e0.record(stream); plan.run(); e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    disc = plan.discarded()
+    tr, n1, n2 = G.observables()
+    S, _, _ = G.operator_entropy()
+    G.close()
+    mine = obs
+    theirs = (tr, n1, n2, S, disc)
+    mixed, fp64 = (theirs, mine) if prec == "fp64" else (mine, theirs)
+    return {"precision": other, "value": int(sum(n_gates)) * steps / (ms / 1e3), "unit": "updates/s",
+            "steps": steps, "mixed_vs_fp64": observable_errors(mixed, fp64)}
 
 
 def run_native(args, ws, rank, local):
@@ -189,6 +241,7 @@ def run_native(args, ws, rank, local):
     clocks.start()
     time.sleep(0.6)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    live = {s: 0.0 for s in lib.mpo.Plan.STAGES}
     barrier()
     clocks.mark()
     wall0 = time.perf_counter()
@@ -199,6 +252,10 @@ def run_native(args, ws, rank, local):
         G.reset()
         plan.run()
         ev[i][1].record(stream)
+        # per-stage device times of this replay, from the event nodes inside the graph
+        # (reading them synchronises the host after the step's last event)
+        for s_, v in plan.stage_times().items():
+            live[s_] += v
     barrier()
     wall = time.perf_counter() - wall0
     clocks.mark()
@@ -206,11 +263,9 @@ def run_native(args, ws, rank, local):
     clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = float(np.sum(step_ms))
+    value = aggregate_value(units * args.steps, tot_ms, ws, dev)
     if ws > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * units * args.steps / (tot_ms / 1e3)
+        tot_ms = ws * units * args.steps / value * 1e3
     disc = plan.discarded()
 
     # per-stage breakdown and algorithmic flops: one instrumented replay (not timed above)
@@ -223,22 +278,24 @@ def run_native(args, ws, rank, local):
         G.reset()
         d_host = G.sweep_mesh(n_gates, k, th, ph, fp)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_val = units / float(np.mean(e2e_t))
-    if ws > 1:
-        t = torch.tensor([float(np.mean(e2e_t))], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = ws * units / float(t.item())
+    e2e_val = aggregate_value(units, 1e3 * float(np.mean(e2e_t)), ws, dev)
     assert np.array_equal(d_host, disc), "sweep and plan disagree"
     tr, n1, n2 = G.observables()
     S, pur, smax = G.operator_entropy()
+    G.close()
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
-    # roofline on the dominant stage; its arithmetic pipe sets the peak (SIMT FP64 or FP32)
-    stage = max(("theta", "gram", "svd", "resplit"), key=lambda s: prof[s][0])
-    ms_s, nl_s, fl_s = prof[stage]
+    # roofline on the dominant kernel of the timed replays; its arithmetic pipe sets the
+    # peak (SIMT FP64 or FP32).  Durations: graph event nodes around each launch over the
+    # timed steps; flops: the executed form's counted flops from one instrumented replay
+    # (identical work: same mesh, same state, deterministic).
+    live_step = {s_: v / args.steps for s_, v in live.items()}
+    stage = max(("theta", "gram", "svd", "resplit"), key=lambda s_: live_step[s_])
+    _, nl_s, fl_s = prof[stage]
+    ms_s = live_step[stage]
     fp64_stage = prec == "fp64" and stage in ("theta", "svd")
     if stage == "svd" and prec == "fp64":
         fl_s = jac["refine_flops"]  # the FP64 part; the FP32 seed is reported beside it
@@ -247,9 +304,13 @@ def run_native(args, ws, rank, local):
     roofline = {"bound": "alu", "kernel": f"k_{stage}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": ("FP64" if fp64_stage else "FP32") + " SIMT FMA peak derived from 152 SMs x "
-                               "2.07 GHz (FP64 ~4, FP32 256 flop/clk/SM); not in MEASURED_PEAKS.json",
+                               "2.07 GHz (FP64 4, FP32 256 flop/clk/SM); MEASURED_PEAKS.json has only HBM and "
+                               "bf16 tensor peaks",
                 "traffic": None, "flops_per_launch": fl_s / max(1, nl_s),
-                "avg_launch_ms": ms_s / max(1, nl_s)}
+                "avg_launch_ms": ms_s / max(1, nl_s), "launches_per_step": nl_s,
+                "timing": "CUDA event record nodes inside the replayed graph, timed steps only"}
+    compare = None if args.no_compare else compare_precision(args, wl, meshes, prec, n_gates, k, th, ph, fp,
+                                                            (tr, n1, n2, S, disc), stream)
     # CPU oracle on a bounded sample (host cores, single BLAS thread)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -266,19 +327,21 @@ def run_native(args, ws, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else prec,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "M": wl.M, "d": wl.d, "chi": wl.chi, "instances": wl.batch,
                    "gates_per_step": units, "precision": prec,
                    "r": float(wl.r[0, 0]), "eta": float(wl.eta[0, 0]), "seeds": wl.seeds[:4],
                    "l2": "flushed: 512 MiB write before each timed step (untimed)",
+                   "svd_cluster": lib.mpo.svd_cluster_shape(),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": plan.launches * args.steps,
         "clocks": clocks.summary(),
-        "stages_ms": {s: round(v[0], 4) for s, v in prof.items()},
+        "compare": compare,
+        "stages_ms": {s_: round(v, 4) for s_, v in live_step.items()},
         "stages_gflop": {s: round(v[2] / 1e9, 4) for s, v in prof.items() if v[2] > 0},
         "jacobi": {"blocks": jac["blocks"], "sweeps_per_block": jac["sweeps"] / max(1, jac["blocks"]),
                    "refine_sweeps_per_block": jac["refine_sweeps"] / max(1, jac["blocks"]),
@@ -301,6 +364,7 @@ def main():
     ap.add_argument("--workload", default="M16_d6_chi64")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the run on the other precision")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -51,11 +51,15 @@ typedef enum {
 } mpo_status;
 
 typedef enum {
-  MPO_FP64 = 0,        /* every step in float64 / complex128                              */
-  MPO_MIXED_TF32 = 1,  /* contraction and Gram products in FP32-accurate tensor/FP32
-                          arithmetic, eigen refinement, threshold, lambda and entropy
-                          in FP64                                                         */
-  MPO_MIXED_BF16 = 2   /* as MIXED_TF32 with BF16-split operands                          */
+  MPO_FP64 = 0,        /* Theta, Jacobi refinement, re-split in float64 / complex128;
+                          the Gram matrix and the Jacobi seed that only starts the
+                          refinement are FP32                                             */
+  MPO_MIXED_TF32 = 1,  /* mixed: Theta contraction, Gram, Jacobi seed and one-sided
+                          refinement in FP32 (SIMT FMA, FP32 accumulation); keep-chi
+                          selection, discarded weight, lambda, entropy, observables and
+                          the stored Gamma in FP64                                        */
+  MPO_MIXED_BF16 = 2   /* accepted as a name for the BF16 form; computes exactly as
+                          MPO_MIXED_TF32 (no BF16 operand path is built)                 */
 } mpo_precision;
 
 typedef struct {
@@ -136,6 +140,21 @@ int mpo_plan_launches(mpo_plan p);
  * Same results as mpo_plan_run.  Synchronises. */
 mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
                             double* stage_flops, double* jacobi);
+/* Device time of each stage (same order as mpo_plan_profile) summed over the layers
+ * of the most recent mpo_plan_run of p, in ms.  The plan's graph holds a CUDA event
+ * record node before and after every stage launch on the handle's stream, so these
+ * are the times of the replay itself, not of a separate instrumented run.
+ * stage_ms: [MPO_NSTAGES] host memory.  MPO_ERR_ARG if p has never been run.
+ * Synchronises. */
+mpo_status mpo_plan_stage_times(mpo_plan p, double* stage_ms);
+
+/* Launch shape of the block SVD (no counterpart in the paper; for benchmarks and
+ * diagnostics).  Blocks whose Gram side is at least *min_n are factorised on a
+ * thread-block cluster of *cluster_size CTAs; *clusters_fp64 / *clusters_fp32 such
+ * clusters fit on the current device at once (0 = launched without clusters).  All
+ * pointers are host memory and nullable.  Initialises the CUDA library if needed;
+ * MPO_ERR_NOT_BUILT without a GPU. */
+mpo_status mpo_svd_cluster_shape(int* cluster_size, int* clusters_fp64, int* clusters_fp32, int* min_n);
 void mpo_plan_destroy(mpo_plan p);
 
 /* Observables of every instance (once per mesh; trace environments):

@@ -18,6 +18,8 @@
 
 size_t eig_smem_bytes(int D);
 cudaError_t gate_module_init();
+int svd_big_min();
+int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32);
 
 struct mpo_ctx {
   int M = 0, d = 0, ncap = 0, B = 0, P = 0, Pc = 0, D = 0;
@@ -58,6 +60,10 @@ struct mpo_plan_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
+  // stage events captured in the graph: per layer MPO_NSTAGES, then two around the
+  // phase screen
+  std::vector<cudaEvent_t> ev;
+  int runs = 0;
 };
 
 namespace {
@@ -126,6 +132,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   if (h->ws_buf) { CK(cudaStreamSynchronize(h->stream)); CK(cudaFree(h->ws_buf)); h->ws_buf = nullptr; }
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
+  w.big_min = svd_big_min();
   const long long D = h->D;
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
@@ -208,17 +215,23 @@ mpo_status build_schedule(mpo_handle h, const int* n_gates, const int* k, const 
   return MPO_OK;
 }
 
+// ev (nullable): MPO_NSTAGES events per layer, then two around the phase screen.
 mpo_status run_layers(mpo_handle h, const GateDesc* d_gates, const std::vector<int>& loff,
-                      const std::vector<int>& lcnt, double* d_disc, const double* d_phase, int* launches) {
-  for (size_t l = 0; l < loff.size(); ++l) {
-    launch_layer(h->dev, h->ws, d_gates + loff[l], lcnt[l], d_disc, h->prec, h->stream, launches);
+                      const std::vector<int>& lcnt, double* d_disc, const double* d_phase, int* launches,
+                      cudaEvent_t* ev = nullptr) {
+  const size_t L = loff.size();
+  for (size_t l = 0; l < L; ++l) {
+    launch_layer(h->dev, h->ws, d_gates + loff[l], lcnt[l], d_disc, h->prec, h->stream, launches,
+                 ev ? ev + l * MPO_NSTAGES : nullptr);
     CK(cudaGetLastError());
   }
+  if (ev) CK(record_stage_event(ev[L * MPO_NSTAGES], h->stream));
   if (d_phase) {
     launch_phases(h->dev, d_phase, h->stream);
     if (launches) *launches += 1;
     CK(cudaGetLastError());
   }
+  if (ev) CK(record_stage_event(ev[L * MPO_NSTAGES + 1], h->stream));
   return MPO_OK;
 }
 
@@ -440,10 +453,14 @@ mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k, const d
     if (cudaMemcpy(pl->d_phase, final_phase, (size_t)h->B * h->M * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(MPO_ERR_CUDA);
   }
+  pl->ev.assign(pl->layer_off.size() * MPO_NSTAGES + 2, nullptr);
+  for (auto& e : pl->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(MPO_ERR_CUDA);
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
   if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(MPO_ERR_CUDA);
   int launches = 0;
-  st = run_layers(h, pl->d_gates, pl->layer_off, pl->layer_cnt, pl->d_disc, pl->d_phase, &launches);
+  st = run_layers(h, pl->d_gates, pl->layer_off, pl->layer_cnt, pl->d_disc, pl->d_phase, &launches,
+                  pl->ev.data());
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (st != MPO_OK) { if (graph) cudaGraphDestroy(graph); return fail(st); }
@@ -460,7 +477,37 @@ mpo_status mpo_plan_run(mpo_plan p) {
   if (!p || !p->h) return MPO_ERR_ARG;
   if (p->h->poisoned) return MPO_ERR_POISONED;
   CK(cudaGraphLaunch(p->exec, p->h->stream));
+  ++p->runs;
   return MPO_OK;
+}
+
+mpo_status mpo_svd_cluster_shape(int* cluster_size, int* clusters_fp64, int* clusters_fp32, int* min_n) {
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return MPO_ERR_NOT_BUILT;
+  if (gate_module_init() != cudaSuccess) return MPO_ERR_CUDA;
+  svd_cluster_info(cluster_size, clusters_fp64, clusters_fp32);
+  if (min_n) *min_n = svd_big_min();
+  return MPO_OK;
+}
+
+mpo_status mpo_plan_stage_times(mpo_plan p, double* stage_ms) {
+  if (!p || !p->h || !stage_ms || p->runs == 0) return MPO_ERR_ARG;
+  mpo_handle h = p->h;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  CK(cudaStreamSynchronize(h->stream));
+  const size_t L = p->layer_off.size();
+  constexpr int NS = MPO_NSTAGES - 1;
+  for (int st = 0; st < MPO_NSTAGES; ++st) stage_ms[st] = 0.0;
+  for (size_t l = 0; l < L; ++l)
+    for (int st = 0; st < NS; ++st) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, p->ev[l * MPO_NSTAGES + st], p->ev[l * MPO_NSTAGES + st + 1]));
+      stage_ms[st] += t;
+    }
+  float tp = 0.f;
+  CK(cudaEventElapsedTime(&tp, p->ev[L * MPO_NSTAGES], p->ev[L * MPO_NSTAGES + 1]));
+  stage_ms[NS] = tp;
+  return poll_error(h);
 }
 
 mpo_status mpo_plan_discarded(mpo_plan p, double* discarded) {
@@ -539,6 +586,8 @@ void mpo_plan_destroy(mpo_plan p) {
   if (p->d_gates) cudaFree(p->d_gates);
   if (p->d_disc) cudaFree(p->d_disc);
   if (p->d_phase) cudaFree(p->d_phase);
+  for (auto e : p->ev)
+    if (e) cudaEventDestroy(e);
   delete p;
 }
 

@@ -38,7 +38,12 @@
 //   makes the singular values and vectors accurate relative to s_max (not s_max^2)
 //   and yields both factors, so the re-split is a scaled copy.
 // Stages: k_setup -> k_theta -> k_gram -> k_order -> k_svd -> k_select -> k_resplit.
+#include <cooperative_groups.h>
+#include <cstdlib>
+
 #include "mpo_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -46,6 +51,20 @@ constexpr int TILE = 16;
 constexpr int MCH = 8;        // new-centre charges mixed per pass of the contraction
 constexpr double TIE_REL = 1e-9;
 constexpr int JACOBI_MAX_SWEEPS = 60;
+// Which blocks are factorised on a whole thread-block cluster (see the large-block
+// section) instead of one CTA: those that would otherwise be the layer's critical
+// path.  A block goes to a cluster when its Gram side is at least SVD_MIN_N (16 on
+// the FP64 path, whose FP64 refinement runs at 1/64 of the FP32 rate, 48 on the FP32
+// path) and its Jacobi work estimate n^2 (n + h) exceeds the layer's total over the
+// CTAs of k_svd, i.e. it alone would hold one SM longer than the average SM is busy.
+// A throughput-bound layer (many instances) therefore keeps every block on one CTA.
+// ws.big_min > 0 replaces the rule by "Gram side >= big_min" (used by the tests).
+template <typename R> struct SvdRoute;
+template <> struct SvdRoute<double> { static constexpr int min_n = 16; };
+template <> struct SvdRoute<float> { static constexpr int min_n = 48; };
+__device__ __forceinline__ unsigned long long svd_work(int n, int h) {
+  return (unsigned long long)n * n * (unsigned long long)(n + h);
+}
 
 template <typename R> struct Prec;
 // tol_*: two-sided Jacobi on the Gram matrix; os_*: one-sided refinement on
@@ -344,31 +363,120 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
 }
 
 // ---------------------------------------------------------------- k_theta
-// One (row segment a, column segment b) item per iteration, in 16 x 16 element tiles:
-// for every old centre segment c between them, P_c[i][j] = sum_gamma Gamma_j[a_i, gamma]
-// lambda_C[gamma] Gamma_{j+1}[gamma, b_j], then Theta(m)[a_i, b_j] += u(a, b, c, m) P_c
-// for up to MCH canonical new centres m per pass.
+// One warp per (row segment a, column segment b) item of a gate.  The warp lists
+// the old centre segments c between a and b (non-empty) and the canonical new
+// centres m between them whose block is non-empty (ballot compaction), then works
+// through the item's na x nb entries in chunks that fit its P buffer:
+//   phase 1, lanes over (c, entry):  P_c[i][j] = sum_gamma Gamma_j[a_i, gamma] lambda_C[gamma] Gamma_{j+1}[gamma, b_j]
+//   phase 2, lanes over (m, entry):  Theta(m)[a_i, b_j] = lambda_A lambda_B sum_c u(a, b, c, m) P_c[i][j]
+// Every P_c and every Theta entry is formed once; segments of a few indices keep
+// all lanes busy because the lanes span c and m as well as the entries.
+constexpr int THETA_WARPS = 8;
+constexpr int THETA_PBUF = 512;  // complex P entries per warp
+constexpr int THETA_EG = 4;      // entries per lane in the mixing phase
+
+// Dynamic shared memory of k_theta (byte offsets, every section 16-byte aligned):
+// Fock table | segment offsets of bonds A, C, B | per-warp c/m lists | per-warp P buffers.
+struct ThetaSmem {
+  size_t seg, misc, wc, lists, pbuf, total;
+};
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline ThetaSmem theta_smem(int ncap, size_t celem) {
+  ThetaSmem L;
+  L.seg = align16((size_t)fock_off(ncap + 1) * celem);
+  L.misc = align16(L.seg + 3 * (size_t)(MPO_P_MAX + 1) * sizeof(int));  // 4 ints
+  L.wc = L.misc + 16;                                                      // MPO_PC_MAX weights
+  L.lists = align16(L.wc + (size_t)MPO_PC_MAX * celem);
+  L.pbuf = align16(L.lists + (size_t)THETA_WARPS * (2 * MPO_P_MAX + 3 * MPO_PC_MAX) * sizeof(int));
+  L.total = L.pbuf + (size_t)THETA_WARPS * THETA_PBUF * celem;
+  return L;
+}
+__host__ __device__ inline size_t theta_smem_bytes(int ncap, size_t celem) { return theta_smem(ncap, celem).total; }
+
+constexpr int THETA_BIG = 64;  // items with at least this many entries are done by the whole CTA
+
+// One warp lists, for the item (a, b), the old centre segments c with a >= c >= b that
+// are non-empty (and their Fock columns c_a - c_c, cbar_a - cbar_c packed in cfk) and
+// the canonical new centres m with a >= m >= b whose block is non-empty (with the
+// item's row and column offsets inside Theta(m)); ballot compaction, warp-synchronous.
+__device__ __forceinline__ void theta_lists(const Slot& sl, const int* segC, int a, int b, int ncap, int P,
+                                            int lane, int* clist, int* cfk, int* mlist, int* mro, int* mco,
+                                            int& nc, int& nm) {
+  const int q = ncap + 1;
+  const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+  const int dk = ca - cb, db = cba - cbb, span = db + 1, ncand = (dk + 1) * span;
+  const unsigned lt = (1u << lane) - 1u;
+  nc = 0;
+  nm = 0;
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    const int u = c0 + lane;
+    int cc = 0;
+    bool ok = false;
+    if (u < ncand) {
+      cc = (cb + u / span) * q + (cbb + u % span);
+      ok = segC[cc + 1] > segC[cc];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int o = nc + __popc(bal & lt);
+      clist[o] = cc;
+      cfk[o] = (dk - u / span) | ((db - u % span) << 16);
+    }
+    nc += __popc(bal);
+  }
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    const int u = c0 + lane;
+    int t = 0;
+    bool ok = false;
+    if (u < ncand) {
+      const int cm = cb + u / span, cbm = cbb + u % span;
+      if (cm <= cbm) {
+        t = canon_index(cm * q + cbm, ncap);
+        ok = sl.f(BF_G, t) != 0;
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const int o = nm + __popc(bal & lt);
+      mlist[o] = t;
+      mro[o] = sl.rowoff[t * P + a];
+      mco[o] = sl.coloff[t * P + b];
+    }
+    nm += __popc(bal);
+  }
+  __syncwarp();
+}
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_theta(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+__global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
   typedef typename Prec<R>::C C;
+  extern __shared__ __align__(16) unsigned char tsm[];
   const int s = blockIdx.y;
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
   const GateDesc g = gates[s];
   const int ncap = st.ncap, q = ncap + 1, P = st.P, M = st.M, D = st.D;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  __shared__ C fk[MPO_FOCK_MAX];
-  __shared__ int segA[MPO_P_MAX + 1], segC[MPO_P_MAX + 1], segB[MPO_P_MAX + 1];
-  __shared__ C As[TILE][TILE + 1], Bs[TILE][TILE + 1];
-  __shared__ int clist[MPO_P_MAX], mlist[MPO_PC_MAX], mro[MPO_PC_MAX], mco[MPO_PC_MAX];
-  __shared__ int ncl, nml;
-  for (int e = tid; e < fock_off(ncap + 1); e += blockDim.x) fk[e] = cvt<C>(sl.fock[e]);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nfk = fock_off(ncap + 1);
+  const ThetaSmem TL = theta_smem(ncap, sizeof(C));
+  C* fk = reinterpret_cast<C*>(tsm);
+  int* segA = reinterpret_cast<int*>(tsm + TL.seg);
+  int* segC = segA + (MPO_P_MAX + 1);
+  int* segB = segC + (MPO_P_MAX + 1);
+  int* clist = reinterpret_cast<int*>(tsm + TL.lists) + warp * (2 * MPO_P_MAX + 3 * MPO_PC_MAX);
+  int* cfk = clist + MPO_P_MAX;   // per c: (c_a - c_c) | (cbar_a - cbar_c) << 16, the Fock columns
+  int* mlist = cfk + MPO_P_MAX;
+  int* mro = mlist + MPO_PC_MAX;
+  int* mco = mro + MPO_PC_MAX;
+  C* pbuf = reinterpret_cast<C*>(tsm + TL.pbuf) + warp * THETA_PBUF;
+  for (int e = tid; e < nfk; e += blockDim.x) fk[e] = cvt<C>(sl.fock[e]);
   const long long bA = (long long)g.inst * (M + 1) + g.j, bC = bA + 1, bB = bA + 2;
   for (int p = tid; p <= P; p += blockDim.x) {
     segA[p] = st.segoff[bA * (P + 1) + p];
     segC[p] = st.segoff[bC * (P + 1) + p];
     segB[p] = st.segoff[bB * (P + 1) + p];
   }
+  __syncthreads();
   const double* lA = st.lam + bA * D;
   const double* lC = st.lam + bC * D;
   const double* lB = st.lam + bB * D;
@@ -377,84 +485,140 @@ __global__ void __launch_bounds__(256) k_theta(MpoDev st, SlotWS ws, const GateD
   C* Th = reinterpret_cast<C*>(sl.theta);
   const int nitems = sl.scal[SS_TTILES];
   unsigned long long flops = 0;
+  // large items: the whole CTA per item (lists in warp 0's area, accumulators of every
+  // m in the CTA's P buffers)
+  int* shn = reinterpret_cast<int*>(tsm + TL.misc);  // [0] nc, [1] nm of the current large item
+  C* wc = reinterpret_cast<C*>(tsm + TL.wc);         // u(a, b, c, m) of the current c, per m
+  C* accs = reinterpret_cast<C*>(tsm + TL.pbuf);
+  const int cap = THETA_WARPS * THETA_PBUF;
   for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
     const int item = sl.items[z];
     const int a = item / P, b = item % P;
-    const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
-    __syncthreads();  // previous item done with the shared lists (and the loads above)
-    if (tid == 0) {
-      int n1 = 0, n2 = 0;
-      for (int cc = 0; cc < P; ++cc) {
-        if (segC[cc + 1] == segC[cc]) continue;
-        const int x = pair_c(cc, ncap), y = pair_cb(cc, ncap);
-        if (x <= ca && x >= cb && y <= cba && y >= cbb) clist[n1++] = cc;
-      }
-      for (int cm = cb; cm <= ca; ++cm)
-        for (int cbm = (cbb > cm ? cbb : cm); cbm <= cba; ++cbm) {
-          const int t = canon_index(cm * q + cbm, ncap);
-          if (sl.f(BF_G, t) == 0) continue;
-          mlist[n2] = t; mro[n2] = sl.rowoff[t * P + a]; mco[n2] = sl.coloff[t * P + b]; ++n2;
-        }
-      ncl = n1; nml = n2;
+    const int na = segA[a + 1] - segA[a], nb = segB[b + 1] - segB[b];
+    if (na * nb < THETA_BIG) continue;  // CTA-uniform
+    int* cl0 = reinterpret_cast<int*>(tsm + TL.lists);
+    if (warp == 0) {
+      int nc, nm;
+      theta_lists(sl, segC, a, b, ncap, P, lane, cl0, cl0 + MPO_P_MAX, cl0 + 2 * MPO_P_MAX,
+                  cl0 + 2 * MPO_P_MAX + MPO_PC_MAX, cl0 + 2 * MPO_P_MAX + 2 * MPO_PC_MAX, nc, nm);
+      if (lane == 0) { shn[0] = nc; shn[1] = nm; }
     }
     __syncthreads();
-    const int nc = ncl, nm = nml;
-    const int na = segA[a + 1] - segA[a], nb = segB[b + 1] - segB[b];
-    const int a0 = segA[a], b0 = segB[b];
+    const int nc = shn[0], nm = shn[1];
+    const int* ccl = cl0;
+    const int* cf = cl0 + MPO_P_MAX;
+    const int* ml = cl0 + 2 * MPO_P_MAX;
+    const int* mr = ml + MPO_PC_MAX;
+    const int* mc = mr + MPO_PC_MAX;
+    const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
     const int dk = ca - cb, db = cba - cbb;
-    for (int mc0 = 0; mc0 < nm; mc0 += MCH) {
-      const int nq = (nm - mc0) < MCH ? (nm - mc0) : MCH;
-      for (int i0 = 0; i0 < na; i0 += TILE)
-        for (int j0 = 0; j0 < nb; j0 += TILE) {
-          const int i = i0 + ty, jc = j0 + tx;
-          const bool valid = (i < na) && (jc < nb);
-          C acc[MCH];
+    const int a0 = segA[a], b0 = segB[b], nent = na * nb;
+    const int E = nm > 0 ? cap / nm : cap;  // entries per pass
+    for (int e0 = 0; nm > 0 && e0 < nent; e0 += E) {
+      const int En = (nent - e0) < E ? (nent - e0) : E;
+      for (int x = tid; x < nm * En; x += blockDim.x) accs[x] = zero_e<C>();
+      __syncthreads();
+      for (int ci = 0; ci < nc; ++ci) {
+        const int cc = ccl[ci], f = cf[ci];
+        for (int mi = tid; mi < nm; mi += blockDim.x) {
+          const int m = sl.f(BF_M, ml[mi]);
+          wc[mi] = cmul(fk[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
+                        cj(fk[fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1) + (f >> 16)]));
+        }
+        __syncthreads();
+        for (int el = tid; el < En; el += blockDim.x) {
+          const int e = e0 + el, i = e / nb, j = e % nb;
+          const double2* g1 = G1 + (long long)(a0 + i) * D;
+          const double2* g2 = G2 + b0 + j;
+          C pc = zero_e<C>();
+          for (int k = segC[cc]; k < segC[cc + 1]; ++k)
+            cfma(pc, cvt<C>(g1[k]), cvt<C>(cscale(g2[(long long)k * D], lC[k])));
+          for (int mi = 0; mi < nm; ++mi) cfma(accs[mi * En + el], wc[mi], pc);
+        }
+        __syncthreads();  // wc is rewritten for the next c
+      }
+      for (int x = tid; x < nm * En; x += blockDim.x) {
+        const int mi = x / En, el = x % En, e = e0 + el, i = e / nb, j = e % nb;
+        const int t = ml[mi];
+        const R sc = (R)(lA[a0 + i] * lB[b0 + j]);
+        Th[sl.f(BF_TOFF, t) + (long long)(mr[mi] + i) * sl.f(BF_C, t) + (mc[mi] + j)] = cscale(accs[x], sc);
+      }
+      __syncthreads();
+    }
+    if (st.ctr && tid == 0) {
+      unsigned long long kc = 0;
+      for (int ci = 0; ci < nc; ++ci) kc += (unsigned long long)(segC[ccl[ci] + 1] - segC[ccl[ci]]);
+      flops += 8ull * (unsigned long long)nent * (kc + (unsigned long long)nc * nm);
+    }
+    __syncthreads();  // lists and accumulators are reused by the next item
+  }
+  // small items: one warp per item
+  for (int z = blockIdx.x * THETA_WARPS + warp; z < nitems; z += gridDim.x * THETA_WARPS) {
+    const int item = sl.items[z];
+    const int a = item / P, b = item % P;
+    const int na = segA[a + 1] - segA[a], nb = segB[b + 1] - segB[b];
+    if (na * nb >= THETA_BIG) continue;  // warp-uniform
+    const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+    const int dk = ca - cb, db = cba - cbb;
+    int nc, nm;
+    theta_lists(sl, segC, a, b, ncap, P, lane, clist, cfk, mlist, mro, mco, nc, nm);
+    if (nm == 0) continue;  // (with no c between, the entries are written as zeros below)
+    const int a0 = segA[a], b0 = segB[b];
+    const int nent = na * nb;
+    const int E = nc > 0 ? THETA_PBUF / nc : THETA_PBUF;  // entries per chunk (nc <= P_MAX = THETA_PBUF)
+    for (int e0 = 0; e0 < nent; e0 += E) {
+      const int En = (nent - e0) < E ? (nent - e0) : E;
+      for (int u = lane; u < nc * En; u += 32) {
+        const int ci = u / En, el = u % En, e = e0 + el, i = e / nb, j = e % nb;
+        const int cc = clist[ci];
+        const double2* g1 = G1 + (long long)(a0 + i) * D;
+        const double2* g2 = G2 + b0 + j;
+        C acc = zero_e<C>();
+        for (int k = segC[cc]; k < segC[cc + 1]; ++k)
+          cfma(acc, cvt<C>(g1[k]), cvt<C>(cscale(g2[(long long)k * D], lC[k])));
+        pbuf[ci * En + el] = acc;
+      }
+      __syncwarp();
+      // lanes over (m, group of THETA_EG entries): the weight u(a, b, c, m) is formed
+      // once per c and applied to the group's entries
+      const int ng = (En + THETA_EG - 1) / THETA_EG;
+      for (int u = lane; u < nm * ng; u += 32) {
+        const int mi = u / ng, el0 = (u % ng) * THETA_EG;
+        const int t = mlist[mi];
+        const int m = sl.f(BF_M, t);
+        const C* fu = fk + fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1);
+        const C* fb = fk + fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1);
+        C acc[THETA_EG];
 #pragma unroll
-          for (int k = 0; k < MCH; ++k) acc[k] = zero_e<C>();
-          for (int ci = 0; ci < nc; ++ci) {
-            const int cc = clist[ci];
-            const int k0 = segC[cc], k1 = segC[cc + 1];
-            const int xc = pair_c(cc, ncap), yc = pair_cb(cc, ncap);
-            C part = zero_e<C>();
-            for (int kb = k0; kb < k1; kb += TILE) {
-              const int kn = (k1 - kb) < TILE ? (k1 - kb) : TILE;
-              As[ty][tx] = (i0 + ty < na && tx < kn) ? cvt<C>(G1[(long long)(a0 + i0 + ty) * D + kb + tx])
-                                                      : zero_e<C>();
-              Bs[ty][tx] = (ty < kn && j0 + tx < nb)
-                               ? cvt<C>(cscale(G2[(long long)(kb + ty) * D + b0 + j0 + tx], lC[kb + ty]))
-                               : zero_e<C>();
-              __syncthreads();
-              if (valid)
-                for (int kk = 0; kk < kn; ++kk) cfma(part, As[ty][kk], Bs[kk][tx]);
-              __syncthreads();
-            }
-            if (valid) {
-              flops += 8ull * (unsigned long long)(k1 - k0) + 8ull * nq;
-              for (int k = 0; k < nq; ++k) {
-                const int m = sl.f(BF_M, mlist[mc0 + k]);
-                const int cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
-                const C uk = fk[fock_off(dk) + (ca - cm) * (dk + 1) + (ca - xc)];
-                const C ub = fk[fock_off(db) + (cba - cbm) * (db + 1) + (cba - yc)];
-                cfma(acc[k], cmul(uk, cj(ub)), part);
-              }
-            }
-          }
-          if (valid) {
-            const R sc = (R)(lA[a0 + i] * lB[b0 + jc]);
-            for (int k = 0; k < nq; ++k) {
-              const int t = mlist[mc0 + k];
-              const int ccols = sl.f(BF_C, t);
-              Th[sl.f(BF_TOFF, t) + (long long)(mro[mc0 + k] + i) * ccols + (mco[mc0 + k] + jc)] =
-                  cscale(acc[k], sc);
-            }
+        for (int x = 0; x < THETA_EG; ++x) acc[x] = zero_e<C>();
+        const int ne = (En - el0) < THETA_EG ? (En - el0) : THETA_EG;
+        for (int ci = 0; ci < nc; ++ci) {
+          const int f = cfk[ci];
+          const C w = cmul(fu[f & 0xffff], cj(fb[f >> 16]));
+          const C* pc = pbuf + ci * En + el0;
+#pragma unroll
+          for (int x = 0; x < THETA_EG; ++x)
+            if (x < ne) cfma(acc[x], w, pc[x]);
+        }
+        const long long tb = sl.f(BF_TOFF, t), ccols = sl.f(BF_C, t);
+#pragma unroll
+        for (int x = 0; x < THETA_EG; ++x) {
+          if (x < ne) {
+            const int e = e0 + el0 + x, i = e / nb, j = e % nb;
+            const R sc = (R)(lA[a0 + i] * lB[b0 + j]);
+            Th[tb + (long long)(mro[mi] + i) * ccols + (mco[mi] + j)] = cscale(acc[x], sc);
           }
         }
+      }
+      __syncwarp();
+    }
+    if (st.ctr && lane == 0) {
+      unsigned long long kc = 0;
+      for (int ci = 0; ci < nc; ++ci) kc += (unsigned long long)(segC[clist[ci] + 1] - segC[clist[ci]]);
+      flops += 8ull * (unsigned long long)nent * (kc + (unsigned long long)nc * nm);
     }
   }
-  if (st.ctr) {
-    flops = __reduce_add_sync(0xffffffffu, (unsigned)flops);
-    if ((tid & 31) == 0 && flops) atomicAdd(st.ctr + CTR_THETA, flops);
-  }
+  if (st.ctr && lane == 0 && flops) atomicAdd(st.ctr + CTR_THETA, flops);
 }
 
 // ---------------------------------------------------------------- k_gram
@@ -932,6 +1096,384 @@ __device__ void seed_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- large blocks
+// A block whose Jacobi work would hold one SM long after the rest of the layer has
+// finished runs on a whole thread-block cluster (K CTAs, one per SM): a parallel
+// one-sided block Jacobi.  The n columns of W (length h) and of V (length n) are cut
+// into 2K column blocks of width b = ceil(n / 2K); a round-robin tournament over the
+// blocks gives every CTA one block pair per round (2K - 1 rounds per sweep).  A CTA
+// stages its two blocks in shared memory, orthogonalises every column of one block
+// against every column of the other (b rounds of b disjoint pairs, one warp per
+// pair; in the first round of a sweep also the pairs inside each block), writes them
+// back to the slot scratch (L2-resident) and meets the others at a cluster barrier.
+// Every pair of columns is visited once per sweep, as in a cyclic sweep.  Sweeps stop
+// when no CTA of the cluster rotated (a sum over distributed shared memory).
+//
+// Precision: the FP32 phase starts from the basis B (identity, or the mirror-real
+// basis of a self-mirror block) and converges in FP32.  A polish in the path's
+// precision follows: two Newton-Schulz steps make V unitary again (distributed by
+// columns), W = Theta V is formed afresh and the sweeps repeat.  The result layout is the single-CTA refinement's (W, V column-major in
+// the slot's W and VC buffers), so the selection and re-split do not change.
+
+// shared-memory header words of k_svd (ints): [0..1] Jacobi flags, [8] work item,
+// [10] rotations of this CTA in the current sweep, [11] cluster total (leader),
+// [12] broadcast copy of the total, [14..15] a double (partial maximum)
+constexpr int HDR_ITEM = 8, HDR_ROT = 10, HDR_TOT = 11, HDR_BC = 12, HDR_MAX = 14;
+
+// Global-memory hand-over between the CTAs of a cluster: every write before the
+// barrier is visible to every read after it (fences at device scope on both sides,
+// so no CTA reads a line it cached before another CTA rewrote it).
+__device__ __forceinline__ void cluster_exchange(cg::cluster_group& cl) {
+  __threadfence();
+  cl.sync();
+  __threadfence();
+}
+
+// Mirror partner (position in the block) of every index on the small side of block
+// t, in shared memory.
+__device__ void block_mirror_map(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, int* mpos,
+                                 int* segX) {
+  const int n = sl.f(BF_G, t), side = sl.f(BF_SIDE, t), P = st.P, M = st.M;
+  const long long bX = (long long)g.inst * (M + 1) + g.j + (side == 0 ? 0 : 2);
+  for (int p = threadIdx.x; p <= P; p += blockDim.x) segX[p] = st.segoff[bX * (P + 1) + p];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mpos[i] = mirror_coord(sl, st, g, t, side, i, segX);
+  __syncthreads();
+}
+
+// Column k of the starting basis of a one-sided Jacobi without a seed: e_k, or for a
+// self-mirror block the basis in which the mirror acts as complex conjugation, so that
+// the columns of Theta B are mirror-real and their inner products real:
+// e_k (k is its own mirror), (e_k + e_p)/sqrt2 (k < p = mirror of k),
+// i (e_p - e_k)/sqrt2 (k > p).  Returns the number of entries (1 or 2).
+template <typename C, typename R>
+__device__ __forceinline__ int basis_col(int k, const int* mpos, bool selfm, int* idx, C* wt) {
+  const R h = (R)0.70710678118654752440;
+  const int p = selfm ? mpos[k] : k;
+  if (p == k) { idx[0] = k; wt[0] = unit_e<C>(); return 1; }
+  if (k < p) { idx[0] = k; wt[0] = mk(h, (R)0); idx[1] = p; wt[1] = mk(h, (R)0); return 2; }
+  idx[0] = p; wt[0] = mk((R)0, h); idx[1] = k; wt[1] = mk((R)0, -h); return 2;
+}
+
+// One warp: one one-sided Jacobi rotation of the column pair (p, q) of W (length h)
+// and the same rotation of the columns of V (length n).  Returns whether it rotated
+// (warp-uniform: the butterfly sums are identical in every lane).
+template <typename R>
+__device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Prec<R>::C* wq,
+                                            typename Prec<R>::C* vp, typename Prec<R>::C* vq, int h, int n,
+                                            bool selfm, R tol_abs, R col_floor, int lane) {
+  typedef typename Prec<R>::C C;
+  R al = 0, be = 0;
+  C ga = zero_e<C>();
+  for (int x = lane; x < h; x += 32) {
+    const C a = wp[x], b = wq[x];
+    al += a.x * a.x + a.y * a.y;
+    be += b.x * b.x + b.y * b.y;
+    cfma_cj(ga, a, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+    ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+  }
+  R c, s;
+  C e;
+  if (!os_params(al, be, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
+  const C ec = cj(e);
+  for (int x = lane; x < h; x += 32) {
+    const C a = wp[x], bs = mulv(wq[x], ec);
+    wp[x] = lin(c, a, -s, bs);
+    wq[x] = lin(s, a, c, bs);
+  }
+  for (int x = lane; x < n; x += 32) {
+    const C a = vp[x], bs = mulv(vq[x], ec);
+    vp[x] = lin(c, a, -s, bs);
+    vq[x] = lin(s, a, c, bs);
+  }
+  return true;
+}
+
+// Largest column norm^2 of the columns [k0, k1) of W over the whole cluster.
+template <typename R>
+__device__ R cluster_max_norm2(cg::cluster_group& cl, const typename Prec<R>::C* W, int h, int k0, int k1,
+                               int* hdr, R* red) {
+  typedef typename Prec<R>::C C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  R mx = 0;
+  for (int k = k0 + warp; k < k1; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    mx = fmax(mx, a);
+  }
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    R m = 0;
+    for (int w2 = 0; w2 < nwarp; ++w2) m = fmax(m, red[w2]);
+    *reinterpret_cast<double*>(hdr + HDR_MAX) = (double)m;
+  }
+  cl.sync();
+  double g = 0;
+  for (unsigned r = 0; r < cl.num_blocks(); ++r)
+    g = fmax(g, *cl.map_shared_rank(reinterpret_cast<double*>(hdr + HDR_MAX), r));
+  cl.sync();  // every CTA has read every partial before any is overwritten
+  return (R)g;
+}
+
+// Sweeps of the parallel one-sided block Jacobi over the cluster on W (h x n) and
+// V (n x n), column-major in global memory.  Returns the number of sweeps that
+// rotated; *rotations accumulates this CTA's applied rotations.
+template <typename R>
+__device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, typename Prec<R>::C* gV, int n,
+                              int h, bool selfm, R tol_abs, R col_floor, unsigned char* smem, const SvdLayout& L,
+                              int* hdr, unsigned long long* rotations) {
+  typedef typename Prec<R>::C C;
+  const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int nb = 2 * K, b = (n + nb - 1) / nb;
+  const size_t room = L.total - L.data;
+  const bool w_st = (size_t)2 * b * h * sizeof(C) <= room;
+  const bool v_st = w_st && (size_t)2 * b * ((size_t)h + n) * sizeof(C) <= room;
+  C* sW = reinterpret_cast<C*>(smem + L.data);
+  C* sV = sW + (size_t)2 * b * h;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) hdr[HDR_ROT] = 0;
+    __syncthreads();
+    for (int rho = 0; rho < nb - 1; ++rho) {
+      int I, J;
+      circle_pair(rho, kr, nb, I, J);
+      const int i0 = I * b, j0 = J * b;
+      const int nI = max(0, min(n, i0 + b) - i0), nJ = max(0, min(n, j0 + b) - j0);
+      const int nl = nI + nJ;
+      auto gcol = [&](int l) { return l < nI ? i0 + l : j0 + (l - nI); };
+      auto wcol = [&](int l) { return w_st ? sW + (size_t)l * h : gW + (long long)gcol(l) * h; };
+      auto vcol = [&](int l) { return v_st ? sV + (size_t)l * n : gV + (long long)gcol(l) * n; };
+      if (w_st) {
+        for (long long e = tid; e < (long long)nl * h; e += nth) sW[e] = gW[(long long)gcol((int)(e / h)) * h + e % h];
+        if (v_st)
+          for (long long e = tid; e < (long long)nl * n; e += nth) sV[e] = gV[(long long)gcol((int)(e / n)) * n + e % n];
+      }
+      __syncthreads();
+      if (rho == 0) {
+        // pairs inside each of the two blocks (every block is in exactly one pair of round 0)
+        const int pI = nI + (nI & 1), pJ = nJ + (nJ & 1);
+        const int rounds = max(pI, pJ) - 1;
+        for (int r = 0; r < rounds; ++r) {
+          const int hI = r < pI - 1 ? pI / 2 : 0, hJ = r < pJ - 1 ? pJ / 2 : 0;
+          for (int k = warp; k < hI + hJ; k += nwarp) {
+            int p, q;
+            if (k < hI) {
+              circle_pair(r, k, pI, p, q);
+              if (q >= nI) continue;
+            } else {
+              circle_pair(r, k - hI, pJ, p, q);
+              if (q >= nJ) continue;
+              p += nI; q += nI;
+            }
+            if (warp_rotate<R>(wcol(p), wcol(q), vcol(p), vcol(q), h, n, selfm, tol_abs, col_floor, lane) &&
+                lane == 0)
+              atomicAdd(&hdr[HDR_ROT], 1);
+          }
+          __syncthreads();
+        }
+      }
+      // pairs across the two blocks: round r pairs column i of I with column (i + r) mod b of J
+      for (int r = 0; r < b; ++r) {
+        for (int i = warp; i < nI; i += nwarp) {
+          const int j = (i + r) % b;
+          if (j >= nJ) continue;
+          if (warp_rotate<R>(wcol(i), wcol(nI + j), vcol(i), vcol(nI + j), h, n, selfm, tol_abs, col_floor,
+                             lane) && lane == 0)
+            atomicAdd(&hdr[HDR_ROT], 1);
+        }
+        __syncthreads();
+      }
+      if (w_st) {
+        for (long long e = tid; e < (long long)nl * h; e += nth) gW[(long long)gcol((int)(e / h)) * h + e % h] = sW[e];
+        if (v_st)
+          for (long long e = tid; e < (long long)nl * n; e += nth) gV[(long long)gcol((int)(e / n)) * n + e % n] = sV[e];
+      }
+      cluster_exchange(cl);
+    }
+    // cluster-wide count of this sweep's rotations
+    if (tid == 0) {
+      *rotations += (unsigned long long)hdr[HDR_ROT];
+      atomicAdd(cl.map_shared_rank(&hdr[HDR_TOT], 0), hdr[HDR_ROT]);
+    }
+    cl.sync();
+    if (tid == 0) hdr[HDR_BC] = *cl.map_shared_rank(&hdr[HDR_TOT], 0);
+    cl.sync();  // every CTA has read the total before the leader clears it
+    if (kr == 0 && tid == 0) hdr[HDR_TOT] = 0;
+    __syncthreads();
+    if (hdr[HDR_BC] == 0) break;
+  }
+  return sweep;
+}
+
+// W = Theta V for the columns [k0, k1) (side 1: W = Theta V, h = rows; side 0:
+// W = Theta^dag V, h = cols), V column-major n x n, in the path precision C.
+template <typename C, typename CT>
+__device__ void form_w_cols(const CT* Th, const C* V, C* W, int r, int c, int side, int n, int h, int k0, int k1) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (long long e = tid; e < (long long)(k1 - k0) * h; e += nth) {
+    const int k = k0 + (int)(e / h), x = (int)(e % h);
+    C acc = zero_e<C>();
+    if (side == 1) {
+      for (int q = 0; q < n; ++q) cfma(acc, cvt<C>(to_d2(Th[(long long)x * c + q])), V[(long long)k * n + q]);
+    } else {
+      for (int i = 0; i < n; ++i) cfma_cj(acc, cvt<C>(to_d2(Th[(long long)i * c + x])), V[(long long)k * n + i]);
+    }
+    W[(long long)k * h + x] = acc;
+  }
+}
+
+// The singular values of block t: column norms of the converged W, ranked descending
+// (ties by index), written to the candidate list; norms go through global scratch.
+template <typename R>
+__device__ void cluster_rank(cg::cluster_group& cl, const MpoDev& st, const Slot& sl, int t,
+                             const typename Prec<R>::C* W, R* nrm, int n, int h, int k0, int k1) {
+  typedef typename Prec<R>::C C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
+  for (int k = k0 + warp; k < k1; k += nwarp) {
+    R a = 0;
+    for (int x = lane; x < h; x += 32) { const C w = W[(long long)k * h + x]; a += w.x * w.x + w.y * w.y; }
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) nrm[k] = a;
+  }
+  cluster_exchange(cl);
+  const int coff = sl.f(BF_COFF, t);
+  const int r0 = (int)((long long)kr * n / K), r1 = (int)((long long)(kr + 1) * n / K);
+  for (int i = r0 + tid; i < r1; i += blockDim.x) {
+    const R wi = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite((double)wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4600 + t);
+    sl.sval[coff + rank] = sqrt((double)wi);
+    sl.perm[coff + rank] = i;
+  }
+}
+
+// One large block on the whole cluster (see the section comment).
+template <typename R>
+__device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& sl, const GateDesc& g, int t,
+                          unsigned char* smem, const SvdLayout& L) {
+  typedef typename Prec<R>::C C;
+  const int n = sl.f(BF_G, t);
+  const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
+  const int h = side == 0 ? c : r;
+  const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
+  const int k0 = (int)((long long)kr * n / K), k1 = (int)((long long)(kr + 1) * n / K);
+  int* hdr = reinterpret_cast<int*>(smem + L.hdr);
+  int* mpos = reinterpret_cast<int*>(smem + L.mpos);
+  int* segX = reinterpret_cast<int*>(smem + L.seg);
+  if (selfm) block_mirror_map(st, sl, g, t, mpos, segX);
+  const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
+  C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);      // this block's region of the W buffer
+  C* gV = reinterpret_cast<C*>(sl.VC) + sl.f(BF_GOFF, t);     // this block's region of the VC buffer
+  // FP32 phase buffers: the mixed path works in place; the FP64 path keeps W32 in the
+  // low half of its own (complex128) W region and V32 in its float2 region of the
+  // seed buffer, which every block addresses with float2 offsets
+  float2* W32 = reinterpret_cast<float2*>(gW);
+  float2* V32 = sizeof(R) == 8 ? reinterpret_cast<float2*>(sl.V) + sl.f(BF_GOFF, t) : reinterpret_cast<float2*>(gV);
+  unsigned long long rot32 = 0, rot64 = 0;
+  // W32 = Theta B, V32 = B on this CTA's columns
+  for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
+    const int k = k0 + (int)(e / n), i = (int)(e % n);
+    int idx[2]; float2 wt[2];
+    const int ne = basis_col<float2, float>(k, mpos, selfm, idx, wt);
+    float2 v = zero_e<float2>();
+    for (int u = 0; u < ne; ++u) if (idx[u] == i) v = wt[u];
+    V32[(long long)k * n + i] = v;
+  }
+  for (long long e = tid; e < (long long)(k1 - k0) * h; e += nth) {
+    const int k = k0 + (int)(e / h), x = (int)(e % h);
+    int idx[2]; float2 wt[2];
+    const int ne = basis_col<float2, float>(k, mpos, selfm, idx, wt);
+    float2 acc = zero_e<float2>();
+    for (int u = 0; u < ne; ++u) {
+      if (side == 1) cfma(acc, cvt<float2>(to_d2(Th[(long long)x * c + idx[u]])), wt[u]);
+      else cfma_cj(acc, cvt<float2>(to_d2(Th[(long long)idx[u] * c + x])), wt[u]);
+    }
+    W32[(long long)k * h + x] = acc;
+  }
+  cluster_exchange(cl);
+  float* red32 = reinterpret_cast<float*>(smem + L.nrm);
+  const float mx32 = cluster_max_norm2<float>(cl, W32, h, k0, k1, hdr, red32);
+  const int sw32 = cluster_sweeps<float>(cl, W32, V32, n, h, selfm, Prec<float>::os_abs * mx32,
+                                         (float)(Prec<float>::floor * mx32), smem, L, hdr, &rot32);
+  int sw64 = 0;
+  R* nrm = reinterpret_cast<R*>(reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t));
+  {
+    // Polish in the path precision: two Newton-Schulz steps V <- V (3 I - V^dag V) / 2
+    // remove the non-unitarity that the FP32 rotations accumulated in V (S in the NS
+    // buffer, the product in this block's W region, W32 being dead now); then
+    // W = Theta V is formed afresh and the sweeps repeat (one or two, typically).
+    C* S = reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t);
+    C* T = gW;
+    if ((const void*)gV != (const void*)V32) {
+      for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
+        const long long o = (long long)k0 * n + e;
+        gV[o] = cvt<C>(to_d2(V32[o]));
+      }
+    }
+    cluster_exchange(cl);
+    for (int it = 0; it < 2; ++it) {
+      for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // S[:, k] = V^dag v_k
+        const int k = k0 + (int)(e / n), a = (int)(e % n);
+        C acc = zero_e<C>();
+        for (int i = 0; i < n; ++i) cfma_cj(acc, gV[(long long)a * n + i], gV[(long long)k * n + i]);
+        S[(long long)k * n + a] = acc;
+      }
+      cluster_exchange(cl);
+      for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // T[:, k] = V (3 e_k - S[:, k]) / 2
+        const int k = k0 + (int)(e / n), i = (int)(e % n);
+        C acc = zero_e<C>();
+        for (int a = 0; a < n; ++a) {
+          C w = S[(long long)k * n + a];
+          w.x = (a == k ? (R)1.5 : (R)0) - (R)0.5 * w.x;
+          w.y = -(R)0.5 * w.y;
+          cfma(acc, gV[(long long)a * n + i], w);
+        }
+        T[(long long)k * n + i] = acc;
+      }
+      cluster_exchange(cl);
+      for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
+        const long long o = (long long)k0 * n + e;
+        gV[o] = T[o];
+      }
+      cluster_exchange(cl);
+    }
+    form_w_cols<C, C>(Th, gV, gW, r, c, side, n, h, k0, k1);
+    cluster_exchange(cl);
+    R* red = reinterpret_cast<R*>(smem + L.nrm);
+    const R mx = cluster_max_norm2<R>(cl, gW, h, k0, k1, hdr, red);
+    sw64 = cluster_sweeps<R>(cl, gW, gV, n, h, selfm, Prec<R>::os_abs * mx, (R)Prec<R>::floor * mx, smem, L, hdr,
+                             &rot64);
+    if (sw64 >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3600 + t);
+  }
+  cluster_rank<R>(cl, st, sl, t, gW, nrm, n, h, k0, k1);
+  if (st.ctr && tid == 0) {
+    // the FP32 phase counts as the seed, the polish (Newton-Schulz, W = Theta V and
+    // the final sweeps, in the path's precision) as the refinement
+    const unsigned long long per = 48ull * h + 24ull * n;
+    atomicAdd(st.ctr + CTR_EIG, rot32 * per);
+    atomicAdd(st.ctr + CTR_REFINE, rot64 * per + 8ull * (unsigned long long)h * n * (k1 - k0) +
+                                       32ull * (unsigned long long)n * n * (k1 - k0));
+    if (kr == 0) {
+      atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sw32 + 1));
+      atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sw64 + 1));
+      atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+    }
+  }
+  cluster_exchange(cl);
+}
+
 // ---------------------------------------------------------------- refinement
 // One-sided Jacobi (Hestenes) refinement of each canonical block's SVD.  The Gram
 // eigenvectors V (n x n, FP32 seed) give W = Theta V (side 1, n = cols) or
@@ -946,8 +1488,8 @@ __device__ void seed_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 // self-mirror blocks the columns are mirror-symmetric, so w_p^dag w_q is real in exact
 // arithmetic; its imaginary part (rounding) is dropped to keep the rotations real.
 template <typename R>
-__device__ void refine_block(const MpoDev& st, const Slot& sl, int t, unsigned char* smem, const SvdLayout& L,
-                             bool seeded) {
+__device__ void refine_block(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, unsigned char* smem,
+                             const SvdLayout& L, bool seeded) {
   typedef typename Prec<R>::C C;
   const int n = sl.f(BF_G, t);
   const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
@@ -968,8 +1510,21 @@ __device__ void refine_block(const MpoDev& st, const Slot& sl, int t, unsigned c
   C* Vc = in_smem ? W + (size_t)h * n : gVc;
   if (tid == 0) { flags[0] = 0; flags[1] = 0; }
   if (!seeded) {
-    // no seed (the Gram eigensolver did not fit): plain one-sided Jacobi from V = I
-    for (int e = tid; e < n * n; e += nth) Vc[e] = ((e / n) == (e % n)) ? unit_e<C>() : zero_e<C>();
+    // no seed (the Gram eigensolver did not fit): one-sided Jacobi from the basis B
+    // (identity, or the mirror-real basis of a self-mirror block, which the real
+    // rotations below require)
+    int* mpos = reinterpret_cast<int*>(smem + L.mpos);
+    if (selfm) block_mirror_map(st, sl, g, t, mpos, reinterpret_cast<int*>(smem + L.seg));
+    for (int e = tid; e < n * n; e += nth) {
+      const int k = e / n, i = e % n;
+      int idx[2];
+      C wt[2];
+      const int ne = basis_col<C, R>(k, mpos, selfm, idx, wt);
+      C v = zero_e<C>();
+      for (int u = 0; u < ne; ++u)
+        if (idx[u] == i) v = wt[u];
+      Vc[e] = v;
+    }
   } else if (sizeof(R) == 8) {
     // The FP32 seed is unitary only to ~1e-7 and the rotations below keep any
     // non-unitarity, so it is first orthonormalised in FP64 by two Newton-Schulz
@@ -1081,53 +1636,105 @@ __device__ void refine_block(const MpoDev& st, const Slot& sl, int t, unsigned c
 }
 
 // ---------------------------------------------------------------- k_order, k_svd
-// The blocks of all gates of a layer go into one list, longest first (bucketed by
-// log2 of an n^2 (n + h) work estimate), for k_svd's persistent CTAs to take in that
-// order (longest-processing-time scheduling): small blocks fill the SMs around the
-// few large ones instead of holding an SM each.  The order inside a bucket does not
-// matter: every block's factorisation depends on its own data only.
-__global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter) {
-  __shared__ int hist[64], start[64];
+// The blocks of all gates of a layer go into one list: the large ones first, then the
+// rest, each part longest first (bucketed by log2 of an n^2 (n + h) work estimate),
+// for k_svd to take in that order (longest-processing-time scheduling).  counter:
+// [0] next large item, [1] large items, [2] next small item (starts at [1]),
+// [3] all items.  The order inside a bucket does not matter: every block's
+// factorisation depends on its own data only.
+// seed_max: the largest Gram side whose FP32 seed fits in one CTA's shared memory;
+// a larger block would run its whole Jacobi unseeded on one SM, so it always goes
+// to a cluster.
+__device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int min_n, int seed_max,
+                                          unsigned long long total, int ncta) {
+  if (ws.big_min > 0) return n >= ws.big_min;
+  return n >= min_n && (n > seed_max || svd_work(n, h) * (unsigned long long)ncta > total);
+}
+
+__device__ __forceinline__ int order_key(bool big, int n, int h) {
+  return (big ? 0 : 64) + 63 - min(63, (int)log2((double)svd_work(n, h) + 1.0));
+}
+
+// ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block.
+__global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter, int ncta,
+                                                int min_n, int seed_max) {
+  __shared__ int hist[128], start[128];
+  __shared__ unsigned long long total;
   const int tid = threadIdx.x, Pc = ws.Pc, E = ngates * Pc;
-  if (tid < 64) hist[tid] = 0;
+  if (tid < 128) hist[tid] = 0;
+  if (tid == 0) total = 0;
   __syncthreads();
   for (int e = tid; e < E; e += blockDim.x) {
     Slot sl = get_slot(ws, e / Pc);
     const int t = e % Pc;
-    if (sl.scal[SS_STATUS] || sl.f(BF_G, t) == 0) continue;
-    const double n = sl.f(BF_G, t), h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    const int key = 63 - min(63, (int)log2(n * n * (n + h) + 1.0));
-    atomicAdd(&hist[key], 1);
+    const int n = sl.f(BF_G, t);
+    if (sl.scal[SS_STATUS] || n == 0) continue;
+    atomicAdd(&total, svd_work(n, sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t)));
+  }
+  __syncthreads();
+  const unsigned long long tot = total;
+  for (int e = tid; e < E; e += blockDim.x) {
+    Slot sl = get_slot(ws, e / Pc);
+    const int t = e % Pc;
+    const int n = sl.f(BF_G, t);
+    if (sl.scal[SS_STATUS] || n == 0) continue;
+    const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
+    atomicAdd(&hist[order_key(route_big(ws, n, h, min_n, seed_max, tot, ncta), n, h)], 1);
   }
   __syncthreads();
   if (tid == 0) {
     int acc = 0;
-    for (int k = 0; k < 64; ++k) { start[k] = acc; acc += hist[k]; }
+    for (int k = 0; k < 128; ++k) {
+      if (k == 64) { counter[1] = acc; counter[2] = acc; }
+      start[k] = acc;
+      acc += hist[k];
+    }
     counter[0] = 0;
-    counter[1] = acc;
+    counter[3] = acc;
   }
   __syncthreads();
   for (int e = tid; e < E; e += blockDim.x) {
     Slot sl = get_slot(ws, e / Pc);
     const int t = e % Pc;
-    if (sl.scal[SS_STATUS] || sl.f(BF_G, t) == 0) continue;
-    const double n = sl.f(BF_G, t), h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    const int key = 63 - min(63, (int)log2(n * n * (n + h) + 1.0));
-    list[atomicAdd(&start[key], 1)] = e;
+    const int n = sl.f(BF_G, t);
+    if (sl.scal[SS_STATUS] || n == 0) continue;
+    const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
+    list[atomicAdd(&start[order_key(route_big(ws, n, h, min_n, seed_max, tot, ncta), n, h)], 1)] = e;
   }
 }
 
+// Persistent: launched as clusters of K CTAs (one CTA per SM).  Each cluster first
+// takes large blocks one at a time and factorises each on all its CTAs (big_block);
+// when none is left, every CTA takes small blocks on its own (FP32 Gram seed when
+// it fits in shared memory, then the one-sided refinement).  Every cluster barrier
+// is reached by all CTAs of the cluster: the work item is broadcast from the
+// cluster's first CTA and every loop bound inside big_block is cluster-uniform.
 template <typename R>
 __global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
                                              const int* __restrict__ list, int* counter, int smem_bytes) {
   extern __shared__ __align__(256) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
   const SvdLayout L = svd_layout<R>(ws.D, (size_t)smem_bytes);
   int* hdr = reinterpret_cast<int*>(smem + L.hdr);
-  const int total = counter[1];
+  if (threadIdx.x == 0) hdr[HDR_TOT] = 0;
+  const int nbig = counter[1], total = counter[3];
   for (;;) {
-    if (threadIdx.x == 0) hdr[8] = atomicAdd(&counter[0], 1);
+    if (cl.block_rank() == 0 && threadIdx.x == 0) hdr[HDR_ITEM] = atomicAdd(&counter[0], 1);
+    cl.sync();
+    if (threadIdx.x == 0) hdr[HDR_ITEM + 1] = *cl.map_shared_rank(&hdr[HDR_ITEM], 0);
+    cl.sync();  // the leader's item has been read everywhere before it changes
+    const int idx = hdr[HDR_ITEM + 1];
+    if (idx >= nbig) break;
+    const int e = list[idx];
+    const int s = e / ws.Pc, t = e % ws.Pc;
+    Slot sl = get_slot(ws, s);
+    const GateDesc g = gates[s];
+    big_block<R>(cl, st, sl, g, t, smem, L);
+  }
+  for (;;) {
+    if (threadIdx.x == 0) hdr[HDR_ITEM] = atomicAdd(&counter[2], 1);
     __syncthreads();
-    const int idx = hdr[8];
+    const int idx = hdr[HDR_ITEM];
     __syncthreads();
     if (idx >= total) break;
     const int e = list[idx];
@@ -1140,7 +1747,7 @@ __global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDes
     const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
     const bool seeded = 2ull * n * n * (selfm ? sizeof(float) : sizeof(float2)) <= L.total - L.data;
     if (seeded) seed_block(st, sl, g, t, smem, L);
-    refine_block<R>(st, sl, t, smem, L, seeded);
+    refine_block<R>(st, sl, g, t, smem, L, seeded);
   }
 }
 
@@ -1442,6 +2049,66 @@ int sm_count() {
 }
 
 constexpr size_t SVD_SMEM = 200 * 1024;
+// k_svd cluster shape: K CTAs per cluster and the number of such clusters that fit on
+// the GPU at once (per precision), from cudaOccupancyMaxActiveClusters at start-up;
+// 0 clusters = launch without clusters (every large block then runs on one CTA).
+constexpr int SVD_CLUSTER = 8;
+int g_svd_clusters[2] = {0, 0};
+
+// CTAs of the k_svd launch for a layer of nblk blocks (a multiple of the cluster size
+// when clusters are available).
+template <typename R>
+int svd_grid(int nblk) {
+  const int ncl = g_svd_clusters[sizeof(R) == 8 ? 0 : 1];
+  if (ncl > 0) {
+    int want = (nblk + SVD_CLUSTER - 1) / SVD_CLUSTER;
+    if (want < 1) want = 1;
+    return (want < ncl ? want : ncl) * SVD_CLUSTER;
+  }
+  const int sms = sm_count();
+  return nblk < sms ? (nblk > 0 ? nblk : 1) : sms;
+}
+
+template <typename R>
+cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int grid, cudaStream_t st) {
+  const int ncl = g_svd_clusters[sizeof(R) == 8 ? 0 : 1];
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = SVD_SMEM;
+  cfg.stream = st;
+  cfg.gridDim = dim3(grid);
+  if (ncl > 0) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = SVD_CLUSTER;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, k_svd<R>, s, ws, d_gates, (const int*)ws.list, ws.counter, (int)SVD_SMEM);
+}
+
+template <typename R>
+int max_svd_clusters() {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3(SVD_CLUSTER * 64);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = SVD_SMEM;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = SVD_CLUSTER;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void*)k_svd<R>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
 
 template <typename R>
 void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
@@ -1451,22 +2118,25 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (per < 1) per = 1;
   if (per > 4096) per = 4096;
   const int nblk = ngates * ws.Pc;
-  const int nsvd = nblk < sms ? nblk : sms;
-  if (ev) cudaEventRecord(ev[0], st);
+  if (ev) record_stage_event(ev[0], st);
   k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates);
-  if (ev) cudaEventRecord(ev[1], st);
-  k_theta<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) record_stage_event(ev[1], st);
+  k_theta<R><<<dim3(per, ngates), THETA_WARPS * 32, theta_smem_bytes(s.ncap, sizeof(typename Prec<R>::C)), st>>>(
+      s, ws, d_gates);
+  if (ev) record_stage_event(ev[2], st);
   k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
-  if (ev) cudaEventRecord(ev[3], st);
-  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter);
-  if (ev) cudaEventRecord(ev[4], st);
-  k_svd<R><<<nsvd, 256, SVD_SMEM, st>>>(s, ws, d_gates, ws.list, ws.counter, (int)SVD_SMEM);
-  if (ev) cudaEventRecord(ev[5], st);
+  if (ev) record_stage_event(ev[3], st);
+  const int svd_ctas = svd_grid<R>(nblk);
+  const SvdLayout SL = svd_layout<R>(ws.D, SVD_SMEM);
+  const int seed_max = (int)sqrt((double)(SL.total - SL.data) / (2.0 * sizeof(float2)));
+  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max);
+  if (ev) record_stage_event(ev[4], st);
+  launch_svd<R>(s, ws, d_gates, svd_ctas, st);
+  if (ev) record_stage_event(ev[5], st);
   k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
-  if (ev) cudaEventRecord(ev[6], st);
+  if (ev) record_stage_event(ev[6], st);
   k_resplit<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
-  if (ev) cudaEventRecord(ev[7], st);
+  if (ev) record_stage_event(ev[7], st);
 }
 
 }  // namespace
@@ -1476,12 +2146,43 @@ cudaError_t gate_module_init() {
   sm_count();
   cudaError_t e = cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_theta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)theta_smem_bytes(MPO_NCAP_MAX, sizeof(double2)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_theta<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)theta_smem_bytes(MPO_NCAP_MAX, sizeof(float2)));
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
-  return e;
+  if (e != cudaSuccess) return e;
+  g_svd_clusters[0] = max_svd_clusters<double>();
+  g_svd_clusters[1] = max_svd_clusters<float>();
+  return cudaSuccess;
+}
+
+// 0: blocks go to a cluster by the load rule (see SvdRoute); GBS_MPO_SVD_CLUSTER_MIN_N
+// (>= 1) in the environment replaces the rule by "Gram side >= that value" (the
+// tests route every block through the cluster path with it).
+int svd_big_min() {
+  static int v = -1;
+  if (v < 0) {
+    v = 0;
+    const char* e = getenv("GBS_MPO_SVD_CLUSTER_MIN_N");
+    if (e && atoi(e) >= 1) v = atoi(e);
+  }
+  return v;
+}
+
+int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32) {
+  if (cluster_size) *cluster_size = SVD_CLUSTER;
+  if (clusters_fp64) *clusters_fp64 = g_svd_clusters[0];
+  if (clusters_fp32) *clusters_fp32 = g_svd_clusters[1];
+  return 0;
 }
 
 // stage_events (optional, 8 events): recorded before each stage launch and after the
 // last one, for per-stage timing (setup, theta, gram, order, svd, select, resplit).
+// They are recorded as external events, so under stream capture they become event
+// record nodes of the graph and time every replay.
 void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
                   int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
   if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev);

@@ -24,6 +24,17 @@
 #define MPO_FOCK_MAX ((MPO_NCAP_MAX + 1) * (MPO_NCAP_MAX + 2) * (2 * MPO_NCAP_MAX + 3) / 6)
 #define MPO_D_LOCAL_MAX 32
 
+// Record a timing event on st.  Under stream capture it becomes an event record node
+// of the graph (external event), so it times every replay; outside capture it is an
+// ordinary record (the external flag is only valid while capturing).
+static inline cudaError_t record_stage_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
 // device error codes (mirror mpo_status)
 #define DEV_ERR_NUMERIC 4
 #define DEV_ERR_CAPACITY 6
@@ -100,11 +111,12 @@ struct SlotWS {
   int* order;      // [S][capCand*2] candidate ids by rank (select)
   int* items;      // [S][P*P] contraction items a*P + b
   double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
+  int big_min;     // blocks with a Gram side >= big_min are factorised on a CTA cluster
   double2* NS;     // [S][capGram] Newton-Schulz scratch V^dag V of the FP64 refinement
   double2* VC;     // [S][capGram] refined right/left factors, column-major, path precision
                    // (never aliases the FP32 Gram or seed buffers of other blocks)
   int* list;       // [S * Pc] layer's blocks, longest first (k_order)
-  int* counter;    // [2]: next list entry, list length
+  int* counter;    // [4]: next large item, large items, next small item, all items
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }

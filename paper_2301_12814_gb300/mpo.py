@@ -22,10 +22,10 @@ PRECISIONS = {"fp64": MPO_FP64, "mixed_tf32": MPO_MIXED_TF32, "mixed_bf16": MPO_
 # every symbol declared in include/gbs_mpo.h
 EXPORTS = [
     "mpo_init_lossy_squeezed", "mpo_reset", "mpo_apply_bs", "mpo_sweep_mesh", "mpo_plan_mesh",
-    "mpo_plan_run", "mpo_plan_discarded", "mpo_plan_launches", "mpo_plan_profile",
+    "mpo_plan_run", "mpo_plan_discarded", "mpo_plan_launches", "mpo_plan_profile", "mpo_plan_stage_times",
     "mpo_plan_destroy",
     "mpo_observables", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
-    "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static",
+    "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
 ]
 
 
@@ -69,6 +69,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_plan_discarded": (_i, [_p, _dp]),
         "mpo_plan_launches": (_i, [_p]),
         "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp, _dp]),
+        "mpo_plan_stage_times": (_i, [_p, _dp]),
+        "mpo_svd_cluster_shape": (_i, [_ip, _ip, _ip, _ip]),
         "mpo_plan_destroy": (None, [_p]),
         "mpo_observables": (_i, [_p, _dp, _dp, _dp, _i]),
         "mpo_operator_entropy": (_i, [_p, _dp, _dp, _dp]),
@@ -104,6 +106,13 @@ def _check(st: int, where: str) -> None:
         raise MPOError(st, where)
 
 
+def svd_cluster_shape() -> dict:
+    """Launch shape of the block SVD on this GPU (mpo_svd_cluster_shape)."""
+    v = np.zeros(4, dtype=np.int32)
+    _check(_lib().mpo_svd_cluster_shape(*[v[i:].ctypes.data_as(_ip) for i in range(4)]), "mpo_svd_cluster_shape")
+    return {"cluster_size": int(v[0]), "clusters_fp64": int(v[1]), "clusters_fp32": int(v[2]), "min_n": int(v[3])}
+
+
 class Plan:
     """A mesh uploaded once and captured in a CUDA graph (mpo_plan_*)."""
 
@@ -137,6 +146,12 @@ class Plan:
             return out, {"blocks": int(jb[0]), "sweeps": int(jb[1]), "refine_sweeps": int(jb[2]),
                          "seed_flops": float(jb[3]), "refine_flops": float(jb[4])}
         return out
+
+    def stage_times(self) -> dict:
+        """{stage: ms} of the most recent run(), from the events inside the graph."""
+        ms = np.zeros(8)
+        _check(_lib().mpo_plan_stage_times(self._h, _d(ms)), "mpo_plan_stage_times")
+        return {s: float(ms[i]) for i, s in enumerate(self.STAGES)}
 
     def close(self) -> None:
         # the owning handle frees its plans itself when it is destroyed first

@@ -121,6 +121,34 @@ def test_chi64_mesh_plan_vs_oracle(lib, chi64_oracle):
     plan.close()
 
 
+def test_plan_stage_times_and_profile(lib, chi64_oracle):
+    """The event nodes inside the plan's graph time every stage of the last replay;
+    the instrumented replay (eager, flop counters) gives the same results."""
+    import torch
+    wl, _ = chi64_oracle
+    mesh = wl.mesh()
+    stream = torch.cuda.Stream()
+    G = lib.MPO(wl.M, wl.d, wl.r[0], wl.eta[0], chi_max=wl.chi, stream=stream)
+    plan = G.plan_mesh([mesh.n_gates], mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
+    with pytest.raises(lib.MPOError):
+        plan.stage_times()          # never run yet
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    G.sync()
+    e0.record(stream); plan.run(); e1.record(stream)
+    st = plan.stage_times()
+    total = e0.elapsed_time(e1)
+    assert all(v >= 0.0 for v in st.values())
+    assert st["svd"] > 0.0 and st["theta"] > 0.0
+    assert sum(st.values()) <= total * 1.05 + 0.05
+    d_plan = plan.discarded()
+    G.reset()
+    prof, jac = plan.profile(with_jacobi=True)
+    assert np.array_equal(plan.discarded(), d_plan)
+    assert prof["svd"][1] == prof["theta"][1] > 0 and prof["svd"][2] > 0
+    assert jac["blocks"] > 0 and jac["refine_flops"] > 0
+    plan.close()
+
+
 def test_chi64_sweep_equals_plan(lib, chi64_oracle):
     wl, _ = chi64_oracle
     mesh = wl.mesh()
@@ -145,9 +173,11 @@ def test_single_gate_api_vs_oracle(lib):
     compare(P, G)
 
 
-def test_batched_instances_bitwise_equal_single(lib):
-    """Independent instances in one handle run in the same layer launches; each must be
-    bit-for-bit the instance run alone (FP64)."""
+def test_batched_instances_equal_single(lib):
+    """Independent instances in one handle run in the same layer launches; each must
+    equal the instance run alone to the FP64 parity bar.  (A block may take the
+    cluster path in one run and the single-CTA path in the other, because that choice
+    depends on the whole layer's load, so equality is not bitwise.)"""
     wl = w.batched_instances(n=3)
     meshes = [wl.mesh(i) for i in range(3)]
     n = [m.n_gates for m in meshes]
@@ -161,11 +191,14 @@ def test_batched_instances_bitwise_equal_single(lib):
     for i in range(3):
         Gi = gpu_handle(lib, wl, insts=(i,))
         di = Gi.sweep_mesh([n[i]], meshes[i].k, meshes[i].theta, meshes[i].phi, meshes[i].final_phase)
-        assert np.array_equal(di, db[off:off + n[i]])
+        assert close(db[off:off + n[i]], di)
         tr, n1, n2 = Gi.observables()
-        assert tr[0] == trb[i] and np.array_equal(n1[0], n1b[i]) and np.array_equal(n2[0], n2b[i])
-        assert np.array_equal(Gi.operator_entropy()[0][0], Sb[i])
+        assert close(trb[i], tr[0]) and close(n1b[i], n1[0]) and close(n2b[i], n2[0])
+        assert close(Sb[i], Gi.operator_entropy()[0][0])
         off += n[i]
+    # the batched run itself is bitwise reproducible
+    Gb.reset()
+    assert np.array_equal(Gb.sweep_mesh(n, k, th, ph, fp), db)
 
 
 def test_batched_instance_vs_oracle(lib):
