@@ -345,7 +345,10 @@ def run_native(args, ws, rank, local):
         "stages_gflop": {s: round(v[2] / 1e9, 4) for s, v in prof.items() if v[2] > 0},
         "jacobi": {"blocks": jac["blocks"], "sweeps_per_block": jac["sweeps"] / max(1, jac["blocks"]),
                    "refine_sweeps_per_block": jac["refine_sweeps"] / max(1, jac["blocks"]),
-                   "seed_gflop_fp32": jac["seed_flops"] / 1e9, "refine_gflop": jac["refine_flops"] / 1e9},
+                   "seed_gflop_fp32": jac["seed_flops"] / 1e9, "refine_gflop": jac["refine_flops"] / 1e9,
+                   "cluster_blocks": jac["cluster_blocks"],
+                   "cluster_ms_per_block": jac["cluster_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6,
+                   "cta_ms_per_block": jac["cta_cycles"] / max(1, jac["blocks"] - jac["cluster_blocks"]) / 2.07e6},
         "wall_s": wall,
         "observables": {"trace": float(tr[0]), "discarded_sum": float(np.sum(disc[:n_gates[0]])),
                         "S_max": float(smax[0])},

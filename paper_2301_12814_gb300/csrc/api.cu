@@ -570,6 +570,9 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
     jacobi[2] = (double)ctr[CTR_RSWEEPS];
     jacobi[3] = (double)ctr[CTR_EIG];
     jacobi[4] = (double)ctr[CTR_REFINE];
+    jacobi[5] = (double)ctr[CTR_NBIG];
+    jacobi[6] = (double)ctr[CTR_CYC_BIG];
+    jacobi[7] = (double)ctr[CTR_CYC_SMALL];
   }
   return poll_error(h);
 }

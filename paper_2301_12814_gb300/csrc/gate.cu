@@ -376,17 +376,17 @@ constexpr int THETA_PBUF = 512;  // complex P entries per warp
 constexpr int THETA_EG = 4;      // entries per lane in the mixing phase
 
 // Dynamic shared memory of k_theta (byte offsets, every section 16-byte aligned):
-// Fock table | segment offsets of bonds A, C, B | per-warp c/m lists | per-warp P buffers.
+// Fock table | segment offsets of bonds A, C, B | 4 ints | per-warp c/m lists |
+// per-warp P buffers (a large item uses all of them together).
 struct ThetaSmem {
-  size_t seg, misc, wc, lists, pbuf, total;
+  size_t seg, misc, lists, pbuf, total;
 };
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline ThetaSmem theta_smem(int ncap, size_t celem) {
   ThetaSmem L;
   L.seg = align16((size_t)fock_off(ncap + 1) * celem);
   L.misc = align16(L.seg + 3 * (size_t)(MPO_P_MAX + 1) * sizeof(int));  // 4 ints
-  L.wc = L.misc + 16;                                                      // MPO_PC_MAX weights
-  L.lists = align16(L.wc + (size_t)MPO_PC_MAX * celem);
+  L.lists = L.misc + 16;
   L.pbuf = align16(L.lists + (size_t)THETA_WARPS * (2 * MPO_P_MAX + 3 * MPO_PC_MAX) * sizeof(int));
   L.total = L.pbuf + (size_t)THETA_WARPS * THETA_PBUF * celem;
   return L;
@@ -394,6 +394,7 @@ __host__ __device__ inline ThetaSmem theta_smem(int ncap, size_t celem) {
 __host__ __device__ inline size_t theta_smem_bytes(int ncap, size_t celem) { return theta_smem(ncap, celem).total; }
 
 constexpr int THETA_BIG = 64;  // items with at least this many entries are done by the whole CTA
+constexpr int THETA_CB = 8;    // c segments per step of a large item
 
 // One warp lists, for the item (a, b), the old centre segments c with a >= c >= b that
 // are non-empty (and their Fock columns c_a - c_c, cbar_a - cbar_c packed in cfk) and
@@ -488,7 +489,6 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
   // large items: the whole CTA per item (lists in warp 0's area, accumulators of every
   // m in the CTA's P buffers)
   int* shn = reinterpret_cast<int*>(tsm + TL.misc);  // [0] nc, [1] nm of the current large item
-  C* wc = reinterpret_cast<C*>(tsm + TL.wc);         // u(a, b, c, m) of the current c, per m
   C* accs = reinterpret_cast<C*>(tsm + TL.pbuf);
   const int cap = THETA_WARPS * THETA_PBUF;
   for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
@@ -513,35 +513,47 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
     const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
     const int dk = ca - cb, db = cba - cbb;
     const int a0 = segA[a], b0 = segB[b], nent = na * nb;
-    const int E = nm > 0 ? cap / nm : cap;  // entries per pass
+    // the CTA's P buffers hold [weights u(c, m) of THETA_CB c's | accumulators of every
+    // m for E entries | P_c of THETA_CB c's for the same entries]
+    const int E = nm > 0 ? (cap - THETA_CB * nm) / (nm + THETA_CB) : cap;  // entries per pass (>= 1)
+    C* wB = accs;
+    C* acc = accs + THETA_CB * nm;
+    C* PB = acc + (size_t)nm * E;
     for (int e0 = 0; nm > 0 && e0 < nent; e0 += E) {
       const int En = (nent - e0) < E ? (nent - e0) : E;
-      for (int x = tid; x < nm * En; x += blockDim.x) accs[x] = zero_e<C>();
-      __syncthreads();
-      for (int ci = 0; ci < nc; ++ci) {
-        const int cc = ccl[ci], f = cf[ci];
-        for (int mi = tid; mi < nm; mi += blockDim.x) {
+      for (int x = tid; x < nm * En; x += blockDim.x) acc[x] = zero_e<C>();
+      for (int c0 = 0; c0 < nc; c0 += THETA_CB) {
+        const int cn = (nc - c0) < THETA_CB ? (nc - c0) : THETA_CB;
+        for (int x = tid; x < cn * nm; x += blockDim.x) {
+          const int cb_ = x / nm, mi = x % nm, f = cf[c0 + cb_];
           const int m = sl.f(BF_M, ml[mi]);
-          wc[mi] = cmul(fk[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
-                        cj(fk[fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1) + (f >> 16)]));
+          wB[cb_ * nm + mi] = cmul(fk[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
+                                   cj(fk[fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1) + (f >> 16)]));
         }
-        __syncthreads();
-        for (int el = tid; el < En; el += blockDim.x) {
-          const int e = e0 + el, i = e / nb, j = e % nb;
+        for (int x = tid; x < cn * En; x += blockDim.x) {
+          const int cb_ = x / En, el = x % En, e = e0 + el, i = e / nb, j = e % nb;
+          const int cc = ccl[c0 + cb_];
           const double2* g1 = G1 + (long long)(a0 + i) * D;
           const double2* g2 = G2 + b0 + j;
           C pc = zero_e<C>();
           for (int k = segC[cc]; k < segC[cc + 1]; ++k)
             cfma(pc, cvt<C>(g1[k]), cvt<C>(cscale(g2[(long long)k * D], lC[k])));
-          for (int mi = 0; mi < nm; ++mi) cfma(accs[mi * En + el], wc[mi], pc);
+          PB[x] = pc;
         }
-        __syncthreads();  // wc is rewritten for the next c
+        __syncthreads();
+        for (int x = tid; x < nm * En; x += blockDim.x) {
+          const int mi = x / En, el = x % En;
+          C a_ = acc[x];
+          for (int cb_ = 0; cb_ < cn; ++cb_) cfma(a_, wB[cb_ * nm + mi], PB[cb_ * En + el]);
+          acc[x] = a_;
+        }
+        __syncthreads();  // wB and PB are rewritten for the next c's
       }
       for (int x = tid; x < nm * En; x += blockDim.x) {
         const int mi = x / En, el = x % En, e = e0 + el, i = e / nb, j = e % nb;
         const int t = ml[mi];
         const R sc = (R)(lA[a0 + i] * lB[b0 + j]);
-        Th[sl.f(BF_TOFF, t) + (long long)(mr[mi] + i) * sl.f(BF_C, t) + (mc[mi] + j)] = cscale(accs[x], sc);
+        Th[sl.f(BF_TOFF, t) + (long long)(mr[mi] + i) * sl.f(BF_C, t) + (mc[mi] + j)] = cscale(acc[x], sc);
       }
       __syncthreads();
     }
@@ -1729,7 +1741,12 @@ __global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDes
     const int s = e / ws.Pc, t = e % ws.Pc;
     Slot sl = get_slot(ws, s);
     const GateDesc g = gates[s];
+    const long long c0 = clock64();
     big_block<R>(cl, st, sl, g, t, smem, L);
+    if (st.ctr && threadIdx.x == 0 && cl.block_rank() == 0) {
+      atomicAdd(st.ctr + CTR_CYC_BIG, (unsigned long long)(clock64() - c0));
+      atomicAdd(st.ctr + CTR_NBIG, 1ull);
+    }
   }
   for (;;) {
     if (threadIdx.x == 0) hdr[HDR_ITEM] = atomicAdd(&counter[2], 1);
@@ -1746,8 +1763,10 @@ __global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDes
     const int n = sl.f(BF_G, t);
     const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
     const bool seeded = 2ull * n * n * (selfm ? sizeof(float) : sizeof(float2)) <= L.total - L.data;
+    const long long c0 = clock64();
     if (seeded) seed_block(st, sl, g, t, smem, L);
     refine_block<R>(st, sl, g, t, smem, L, seeded);
+    if (st.ctr && threadIdx.x == 0) atomicAdd(st.ctr + CTR_CYC_SMALL, (unsigned long long)(clock64() - c0));
   }
 }
 

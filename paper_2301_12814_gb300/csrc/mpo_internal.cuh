@@ -54,7 +54,8 @@ struct MpoDev {
 };
 
 // algorithmic work counters (real flops of the executed form)
-enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS, CTR_N };
+enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS,
+       CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_N };
 
 struct GateDesc {
   int inst, j, out, pad;

@@ -302,7 +302,7 @@ def mixed_errors(P, G):
             "tr_abs": float(abs(gtr[0] - tr))}
 
 
-@pytest.mark.parametrize("name,ngates", [("M16_d6_chi64", None), ("M32_d8_chi256", 24)])
+@pytest.mark.parametrize("name,ngates", [("M16_d6_chi64", None), ("M32_d8_chi256", 24), ("M48_d8_chi512", 6)])
 def test_mixed_precision_vs_oracle(lib, name, ngates):
     wl = w.workload(name)
     mesh = wl.mesh()
