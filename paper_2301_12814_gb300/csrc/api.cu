@@ -19,6 +19,7 @@
 size_t eig_smem_bytes(int D);
 cudaError_t gate_module_init();
 int svd_big_min();
+int svd_cluster_seed_max();
 int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32);
 
 struct mpo_ctx {
@@ -133,6 +134,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
   w.big_min = svd_big_min();
+  w.cl_seed_max = svd_cluster_seed_max();
   const long long D = h->D;
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
@@ -573,6 +575,9 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
     jacobi[5] = (double)ctr[CTR_NBIG];
     jacobi[6] = (double)ctr[CTR_CYC_BIG];
     jacobi[7] = (double)ctr[CTR_CYC_SMALL];
+    jacobi[8] = (double)ctr[CTR_CYC_SEED];
+    jacobi[9] = (double)ctr[CTR_CYC_NS];
+    jacobi[10] = (double)ctr[CTR_CYC_POLISH];
   }
   return poll_error(h);
 }

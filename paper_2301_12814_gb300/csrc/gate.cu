@@ -70,14 +70,19 @@ template <typename R> struct Prec;
 // tol_*: two-sided Jacobi on the Gram matrix; os_*: one-sided refinement on
 // W = Theta V; floor: singular values with s^2 <= floor * s_max^2 are dropped (the
 // refined values are accurate to a few ulps of s_max, not of s_max^2).
+// stop2: once the largest relative off-diagonal |w_p^dag w_q|^2 / (|w_p|^2 |w_q|^2) of a
+// one-sided sweep is below stop2, the quadratically convergent next sweep could only
+// apply rotations below the tolerance, so the iteration stops after this sweep.
 template <> struct Prec<double> {
   typedef double2 C;
+  static constexpr double stop2 = 1e-16;
   static constexpr double tol_rel = 1e-15, tol_abs = 1e-18;
   static constexpr double os_rel = 4e-15, os_abs = 1e-30;
   static constexpr double floor = 1e-28;
 };
 template <> struct Prec<float> {
   typedef float2 C;
+  static constexpr double stop2 = 1e-10;
   // off-diagonals below ~3 FP32 ulps of the largest diagonal are rounding noise
   static constexpr float tol_rel = 2e-7f, tol_abs = 2e-7f;
   static constexpr float os_rel = 2e-6f, os_abs = 1e-13f;
@@ -394,7 +399,6 @@ __host__ __device__ inline ThetaSmem theta_smem(int ncap, size_t celem) {
 __host__ __device__ inline size_t theta_smem_bytes(int ncap, size_t celem) { return theta_smem(ncap, celem).total; }
 
 constexpr int THETA_BIG = 64;  // items with at least this many entries are done by the whole CTA
-constexpr int THETA_CB = 8;    // c segments per step of a large item
 
 // One warp lists, for the item (a, b), the old centre segments c with a >= c >= b that
 // are non-empty (and their Fock columns c_a - c_c, cbar_a - cbar_c packed in cfk) and
@@ -486,11 +490,10 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
   C* Th = reinterpret_cast<C*>(sl.theta);
   const int nitems = sl.scal[SS_TTILES];
   unsigned long long flops = 0;
-  // large items: the whole CTA per item (lists in warp 0's area, accumulators of every
-  // m in the CTA's P buffers)
+  // large items: the whole CTA per item (lists in warp 0's area, the Gamma tiles in
+  // the CTA's P buffers)
   int* shn = reinterpret_cast<int*>(tsm + TL.misc);  // [0] nc, [1] nm of the current large item
   C* accs = reinterpret_cast<C*>(tsm + TL.pbuf);
-  const int cap = THETA_WARPS * THETA_PBUF;
   for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
     const int item = sl.items[z];
     const int a = item / P, b = item % P;
@@ -513,49 +516,62 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
     const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap), cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
     const int dk = ca - cb, db = cba - cbb;
     const int a0 = segA[a], b0 = segB[b], nent = na * nb;
-    // the CTA's P buffers hold [weights u(c, m) of THETA_CB c's | accumulators of every
-    // m for E entries | P_c of THETA_CB c's for the same entries]
-    const int E = nm > 0 ? (cap - THETA_CB * nm) / (nm + THETA_CB) : cap;  // entries per pass (>= 1)
-    C* wB = accs;
-    C* acc = accs + THETA_CB * nm;
-    C* PB = acc + (size_t)nm * E;
-    for (int e0 = 0; nm > 0 && e0 < nent; e0 += E) {
-      const int En = (nent - e0) < E ? (nent - e0) : E;
-      for (int x = tid; x < nm * En; x += blockDim.x) acc[x] = zero_e<C>();
-      for (int c0 = 0; c0 < nc; c0 += THETA_CB) {
-        const int cn = (nc - c0) < THETA_CB ? (nc - c0) : THETA_CB;
-        for (int x = tid; x < cn * nm; x += blockDim.x) {
-          const int cb_ = x / nm, mi = x % nm, f = cf[c0 + cb_];
-          const int m = sl.f(BF_M, ml[mi]);
-          wB[cb_ * nm + mi] = cmul(fk[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
+    // 16 x 16 entry tiles, one thread per entry; for each c the Gamma tiles are staged
+    // in shared memory (each element loaded once per tile) and P_c is mixed into the
+    // accumulators of up to TMCH canonical m held in registers (P_c is recomputed for
+    // every further group of TMCH m)
+    constexpr int TMCH = sizeof(R) == 8 ? 8 : 16;
+    C (*As)[TILE + 1] = reinterpret_cast<C (*)[TILE + 1]>(accs);
+    C (*Bs)[TILE + 1] = reinterpret_cast<C (*)[TILE + 1]>(accs + TILE * (TILE + 1));
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int mc0 = 0; mc0 < nm; mc0 += TMCH) {
+      const int nq = (nm - mc0) < TMCH ? (nm - mc0) : TMCH;
+      for (int i0 = 0; i0 < na; i0 += TILE)
+        for (int j0 = 0; j0 < nb; j0 += TILE) {
+          const int i = i0 + ty, jc = j0 + tx;
+          const bool valid = (i < na) && (jc < nb);
+          C acc[TMCH];
+#pragma unroll
+          for (int k = 0; k < TMCH; ++k) acc[k] = zero_e<C>();
+          for (int ci = 0; ci < nc; ++ci) {
+            const int cc = ccl[ci], f = cf[ci];
+            const int k0 = segC[cc], k1 = segC[cc + 1];
+            C part = zero_e<C>();
+            for (int kb = k0; kb < k1; kb += TILE) {
+              const int kn = (k1 - kb) < TILE ? (k1 - kb) : TILE;
+              As[ty][tx] = (i0 + ty < na && tx < kn) ? cvt<C>(G1[(long long)(a0 + i0 + ty) * D + kb + tx]) : zero_e<C>();
+              Bs[ty][tx] = (ty < kn && j0 + tx < nb)
+                               ? cvt<C>(cscale(G2[(long long)(kb + ty) * D + b0 + j0 + tx], lC[kb + ty]))
+                               : zero_e<C>();
+              __syncthreads();
+              if (valid)
+                for (int kk = 0; kk < kn; ++kk) cfma(part, As[ty][kk], Bs[kk][tx]);
+              __syncthreads();
+            }
+            if (valid) {
+#pragma unroll
+              for (int k = 0; k < TMCH; ++k) {
+                if (k < nq) {
+                  const int m = sl.f(BF_M, ml[mc0 + k]);
+                  const C w = cmul(fk[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
                                    cj(fk[fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1) + (f >> 16)]));
+                  cfma(acc[k], w, part);
+                }
+              }
+            }
+          }
+          if (valid) {
+            const R sc = (R)(lA[a0 + i] * lB[b0 + jc]);
+#pragma unroll
+            for (int k = 0; k < TMCH; ++k) {
+              if (k < nq) {
+                const int t = ml[mc0 + k];
+                Th[sl.f(BF_TOFF, t) + (long long)(mr[mc0 + k] + i) * sl.f(BF_C, t) + (mc[mc0 + k] + jc)] =
+                    cscale(acc[k], sc);
+              }
+            }
+          }
         }
-        for (int x = tid; x < cn * En; x += blockDim.x) {
-          const int cb_ = x / En, el = x % En, e = e0 + el, i = e / nb, j = e % nb;
-          const int cc = ccl[c0 + cb_];
-          const double2* g1 = G1 + (long long)(a0 + i) * D;
-          const double2* g2 = G2 + b0 + j;
-          C pc = zero_e<C>();
-          for (int k = segC[cc]; k < segC[cc + 1]; ++k)
-            cfma(pc, cvt<C>(g1[k]), cvt<C>(cscale(g2[(long long)k * D], lC[k])));
-          PB[x] = pc;
-        }
-        __syncthreads();
-        for (int x = tid; x < nm * En; x += blockDim.x) {
-          const int mi = x / En, el = x % En;
-          C a_ = acc[x];
-          for (int cb_ = 0; cb_ < cn; ++cb_) cfma(a_, wB[cb_ * nm + mi], PB[cb_ * En + el]);
-          acc[x] = a_;
-        }
-        __syncthreads();  // wB and PB are rewritten for the next c's
-      }
-      for (int x = tid; x < nm * En; x += blockDim.x) {
-        const int mi = x / En, el = x % En, e = e0 + el, i = e / nb, j = e % nb;
-        const int t = ml[mi];
-        const R sc = (R)(lA[a0 + i] * lB[b0 + j]);
-        Th[sl.f(BF_TOFF, t) + (long long)(mr[mi] + i) * sl.f(BF_C, t) + (mc[mi] + j)] = cscale(acc[x], sc);
-      }
-      __syncthreads();
     }
     if (st.ctr && tid == 0) {
       unsigned long long kc = 0;
@@ -837,6 +853,18 @@ __device__ __forceinline__ bool os_params(float al, float be, float2 ga, bool se
   return true;
 }
 
+// Relative off-diagonal |g|^2 / (a b) of a column pair, in FP32 (it only steers the
+// sweep stop).  The FP64 version rescales all three by the same power of two taken
+// from a's exponent bits, so the FP32 quotient neither divides in FP64 nor underflows
+// (b >= the column floor, a fraction >= 1e-28 of the largest column).
+__device__ __forceinline__ float rel_off2(float a, float b, float g2) { return g2 / (a * b); }
+__device__ __forceinline__ float rel_off2(double a, double b, double g2) {
+  const int e = ((__double2hiint(a) >> 20) & 0x7ff) - 1023;
+  const double sc = __hiloint2double((1023 - e) << 20, 0);  // 2^-e
+  const float fa = (float)(a * sc), fb = (float)(b * sc), fg = (float)(g2 * sc * sc);
+  return fg / (fa * fb);
+}
+
 template <typename R> struct PairWork {
   R al, be, c, s;
   typename Prec<R>::C ga, e;
@@ -855,8 +883,9 @@ __device__ int refine_sweeps_fp32(float2* W, float2* Vc, int n, int h, bool self
   int sweep = 0;
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     __syncthreads();
-    if (tid == 0) flags[0] = 0;
+    if (tid == 0) { flags[0] = 0; flags[2] = 0; }
     __syncthreads();
+    float wr2 = 0.f;
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       for (int k = warp; k < half; k += nwarp) {
         int p, qq;
@@ -878,6 +907,8 @@ __device__ int refine_sweeps_fp32(float2* W, float2* Vc, int n, int h, bool self
           ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
           ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
         }
+        if (al > col_floor && be > col_floor)
+          wr2 = fmaxf(wr2, rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y));
         float c, sn;
         float2 e;
         if (!os_params(al, be, ga, selfm, tol_abs, col_floor, c, sn, e)) continue;  // warp-uniform
@@ -898,7 +929,10 @@ __device__ int refine_sweeps_fp32(float2* W, float2* Vc, int n, int h, bool self
       }
       __syncthreads();
     }
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(wr2));
+    __syncthreads();
     if (!flags[0]) break;
+    if ((double)__uint_as_float((unsigned)flags[2]) < Prec<float>::stop2) { ++sweep; break; }
   }
   __syncthreads();
   return sweep;
@@ -913,7 +947,7 @@ __device__ int refine_sweeps(typename Prec<R>::C* W, typename Prec<R>::C* Vc, in
   int sweep = 0;
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     __syncthreads();
-    if (tid == 0) flags[0] = 0;
+    if (tid == 0) { flags[0] = 0; flags[2] = 0; }
     __syncthreads();
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       for (int c0 = 0; c0 < half; c0 += PAIR_CHUNK) {
@@ -943,6 +977,12 @@ __device__ int refine_sweeps(typename Prec<R>::C* W, typename Prec<R>::C* Vc, in
         __syncthreads();
         for (int k = tid; k < cn; k += nth) {
           if (!pw[k].act) continue;
+          const R al = pw[k].al, be = pw[k].be;
+          if (al > col_floor && be > col_floor) {
+            const C ga = pw[k].ga;
+            const float r2 = rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y);
+            atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(r2));
+          }
           R c, s;
           C e;
           if (os_params(pw[k].al, pw[k].be, pw[k].ga, selfm, tol_abs, col_floor, c, s, e)) {
@@ -979,6 +1019,7 @@ __device__ int refine_sweeps(typename Prec<R>::C* W, typename Prec<R>::C* Vc, in
       }
     }
     if (!flags[0]) break;
+    if ((double)__uint_as_float((unsigned)flags[2]) < Prec<R>::stop2) { ++sweep; break; }
   }
   __syncthreads();
   return sweep;
@@ -1009,7 +1050,7 @@ __host__ __device__ inline SvdLayout svd_layout(int D, size_t total) {
   SvdLayout L;
   size_t o = 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  L.hdr = o; o = al(o + 64);
+  L.hdr = o; o = al(o + 128);  // 32 ints (Jacobi flags, work item, cluster sweep totals)
   const size_t pwb = (size_t)PAIR_CHUNK * sizeof(PairWork<R>);
   const size_t rtb = (size_t)PAIR_CHUNK * sizeof(Rot<float, float2>);
   L.pw = o; o = al(o + (pwb > rtb ? pwb : rtb));
@@ -1131,6 +1172,7 @@ __device__ void seed_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 // [10] rotations of this CTA in the current sweep, [11] cluster total (leader),
 // [12] broadcast copy of the total, [14..15] a double (partial maximum)
 constexpr int HDR_ITEM = 8, HDR_ROT = 10, HDR_TOT = 11, HDR_BC = 12, HDR_MAX = 14;
+constexpr int HDR_RMAX = 16, HDR_RTOT = 17, HDR_RBC = 18;  // largest relative off-diagonal^2 of a sweep
 
 // Global-memory hand-over between the CTAs of a cluster: every write before the
 // barrier is visible to every read after it (fences at device scope on both sides,
@@ -1173,7 +1215,7 @@ __device__ __forceinline__ int basis_col(int k, const int* mpos, bool selfm, int
 template <typename R>
 __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Prec<R>::C* wq,
                                             typename Prec<R>::C* vp, typename Prec<R>::C* vq, int h, int n,
-                                            bool selfm, R tol_abs, R col_floor, int lane) {
+                                            bool selfm, R tol_abs, R col_floor, int lane, float& r2) {
   typedef typename Prec<R>::C C;
   R al = 0, be = 0;
   C ga = zero_e<C>();
@@ -1189,6 +1231,8 @@ __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Pr
     ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
     ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
   }
+  r2 = (al > col_floor && be > col_floor) ? rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y)
+                                          : 0.f;
   R c, s;
   C e;
   if (!os_params(al, be, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
@@ -1251,8 +1295,10 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
   C* sW = reinterpret_cast<C*>(smem + L.data);
   C* sV = sW + (size_t)2 * b * h;
   int sweep = 0;
+  float wr2 = 0.f;  // this warp's largest relative off-diagonal^2 in the sweep
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
-    if (tid == 0) hdr[HDR_ROT] = 0;
+    if (tid == 0) { hdr[HDR_ROT] = 0; hdr[HDR_RMAX] = 0; }
+    wr2 = 0.f;
     __syncthreads();
     for (int rho = 0; rho < nb - 1; ++rho) {
       int I, J;
@@ -1263,6 +1309,13 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
       auto gcol = [&](int l) { return l < nI ? i0 + l : j0 + (l - nI); };
       auto wcol = [&](int l) { return w_st ? sW + (size_t)l * h : gW + (long long)gcol(l) * h; };
       auto vcol = [&](int l) { return v_st ? sV + (size_t)l * n : gV + (long long)gcol(l) * n; };
+      auto rotate = [&](int p, int q) {
+        float r2 = 0.f;
+        const bool rot =
+            warp_rotate<R>(wcol(p), wcol(q), vcol(p), vcol(q), h, n, selfm, tol_abs, col_floor, lane, r2);
+        wr2 = fmaxf(wr2, r2);
+        if (rot && lane == 0) atomicAdd(&hdr[HDR_ROT], 1);
+      };
       if (w_st) {
         for (long long e = tid; e < (long long)nl * h; e += nth) sW[e] = gW[(long long)gcol((int)(e / h)) * h + e % h];
         if (v_st)
@@ -1285,9 +1338,7 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
               if (q >= nJ) continue;
               p += nI; q += nI;
             }
-            if (warp_rotate<R>(wcol(p), wcol(q), vcol(p), vcol(q), h, n, selfm, tol_abs, col_floor, lane) &&
-                lane == 0)
-              atomicAdd(&hdr[HDR_ROT], 1);
+            rotate(p, q);
           }
           __syncthreads();
         }
@@ -1297,9 +1348,7 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
         for (int i = warp; i < nI; i += nwarp) {
           const int j = (i + r) % b;
           if (j >= nJ) continue;
-          if (warp_rotate<R>(wcol(i), wcol(nI + j), vcol(i), vcol(nI + j), h, n, selfm, tol_abs, col_floor,
-                             lane) && lane == 0)
-            atomicAdd(&hdr[HDR_ROT], 1);
+          rotate(i, nI + j);
         }
         __syncthreads();
       }
@@ -1310,17 +1359,24 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
       }
       cluster_exchange(cl);
     }
-    // cluster-wide count of this sweep's rotations
+    // cluster-wide count of this sweep's rotations and its largest relative off-diagonal
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(&hdr[HDR_RMAX]), __float_as_uint(wr2));
+    __syncthreads();
     if (tid == 0) {
       *rotations += (unsigned long long)hdr[HDR_ROT];
       atomicAdd(cl.map_shared_rank(&hdr[HDR_TOT], 0), hdr[HDR_ROT]);
+      atomicMax(cl.map_shared_rank(reinterpret_cast<unsigned*>(&hdr[HDR_RTOT]), 0), (unsigned)hdr[HDR_RMAX]);
     }
     cl.sync();
-    if (tid == 0) hdr[HDR_BC] = *cl.map_shared_rank(&hdr[HDR_TOT], 0);
-    cl.sync();  // every CTA has read the total before the leader clears it
-    if (kr == 0 && tid == 0) hdr[HDR_TOT] = 0;
+    if (tid == 0) {
+      hdr[HDR_BC] = *cl.map_shared_rank(&hdr[HDR_TOT], 0);
+      hdr[HDR_RBC] = *cl.map_shared_rank(&hdr[HDR_RTOT], 0);
+    }
+    cl.sync();  // every CTA has read the totals before the leader clears them
+    if (kr == 0 && tid == 0) { hdr[HDR_TOT] = 0; hdr[HDR_RTOT] = 0; }
     __syncthreads();
     if (hdr[HDR_BC] == 0) break;
+    if ((double)__uint_as_float((unsigned)hdr[HDR_RBC]) < Prec<R>::stop2) { ++sweep; break; }
   }
   return sweep;
 }
@@ -1372,7 +1428,7 @@ __device__ void cluster_rank(cg::cluster_group& cl, const MpoDev& st, const Slot
 // One large block on the whole cluster (see the section comment).
 template <typename R>
 __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& sl, const GateDesc& g, int t,
-                          unsigned char* smem, const SvdLayout& L) {
+                          unsigned char* smem, const SvdLayout& L, int ws_cl_seed_max) {
   typedef typename Prec<R>::C C;
   const int n = sl.f(BF_G, t);
   const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
@@ -1394,6 +1450,27 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
   float2* W32 = reinterpret_cast<float2*>(gW);
   float2* V32 = sizeof(R) == 8 ? reinterpret_cast<float2*>(sl.V) + sl.f(BF_GOFF, t) : reinterpret_cast<float2*>(gV);
   unsigned long long rot32 = 0, rot64 = 0;
+  // A block small enough takes the FP32 Gram seed (two-sided Jacobi in the shared
+  // memory of the cluster's first CTA, written row-major to the seed buffer) instead
+  // of the FP32 one-sided phase: a few hundred CTA-local rounds in place of ~8
+  // sweeps of cluster rounds.
+  const bool gram_seed =
+      n <= ws_cl_seed_max && 2ull * n * n * (selfm ? sizeof(float) : sizeof(float2)) <= L.total - L.data;
+  const float2* Vs = reinterpret_cast<const float2*>(sl.V) + sl.f(BF_GOFF, t);
+  int sw32 = 0;
+  const bool timed = st.ctr && kr == 0 && tid == 0;
+  long long tc = timed ? clock64() : 0;
+  auto lap = [&](int ctr) {
+    if (timed) {
+      const long long now = clock64();
+      atomicAdd(st.ctr + ctr, (unsigned long long)(now - tc));
+      tc = now;
+    }
+  };
+  if (gram_seed) {
+    if (kr == 0) seed_block(st, sl, g, t, smem, L);
+    cluster_exchange(cl);
+  } else {
   // W32 = Theta B, V32 = B on this CTA's columns
   for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
     const int k = k0 + (int)(e / n), i = (int)(e % n);
@@ -1417,8 +1494,10 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
   cluster_exchange(cl);
   float* red32 = reinterpret_cast<float*>(smem + L.nrm);
   const float mx32 = cluster_max_norm2<float>(cl, W32, h, k0, k1, hdr, red32);
-  const int sw32 = cluster_sweeps<float>(cl, W32, V32, n, h, selfm, Prec<float>::os_abs * mx32,
-                                         (float)(Prec<float>::floor * mx32), smem, L, hdr, &rot32);
+  sw32 = cluster_sweeps<float>(cl, W32, V32, n, h, selfm, Prec<float>::os_abs * mx32,
+                               (float)(Prec<float>::floor * mx32), smem, L, hdr, &rot32);
+  }
+  lap(CTR_CYC_SEED);
   int sw64 = 0;
   R* nrm = reinterpret_cast<R*>(reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t));
   {
@@ -1428,7 +1507,12 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
     // W = Theta V is formed afresh and the sweeps repeat (one or two, typically).
     C* S = reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t);
     C* T = gW;
-    if ((const void*)gV != (const void*)V32) {
+    if (gram_seed) {
+      for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // column-major from row-major
+        const int k = k0 + (int)(e / n), i = (int)(e % n);
+        gV[(long long)k * n + i] = cvt<C>(to_d2(Vs[(long long)i * n + k]));
+      }
+    } else if ((const void*)gV != (const void*)V32) {
       for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
         const long long o = (long long)k0 * n + e;
         gV[o] = cvt<C>(to_d2(V32[o]));
@@ -1461,6 +1545,7 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
       }
       cluster_exchange(cl);
     }
+    lap(CTR_CYC_NS);
     form_w_cols<C, C>(Th, gV, gW, r, c, side, n, h, k0, k1);
     cluster_exchange(cl);
     R* red = reinterpret_cast<R*>(smem + L.nrm);
@@ -1469,6 +1554,7 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
                              &rot64);
     if (sw64 >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3600 + t);
   }
+  lap(CTR_CYC_POLISH);
   cluster_rank<R>(cl, st, sl, t, gW, nrm, n, h, k0, k1);
   if (st.ctr && tid == 0) {
     // the FP32 phase counts as the seed, the polish (Newton-Schulz, W = Theta V and
@@ -1478,9 +1564,11 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
     atomicAdd(st.ctr + CTR_REFINE, rot64 * per + 8ull * (unsigned long long)h * n * (k1 - k0) +
                                        32ull * (unsigned long long)n * n * (k1 - k0));
     if (kr == 0) {
-      atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sw32 + 1));
+      if (!gram_seed) {  // (seed_block counts its own sweeps and block)
+        atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sw32 + 1));
+        atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+      }
       atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sw64 + 1));
-      atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
     }
   }
   cluster_exchange(cl);
@@ -1722,13 +1810,13 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
 // is reached by all CTAs of the cluster: the work item is broadcast from the
 // cluster's first CTA and every loop bound inside big_block is cluster-uniform.
 template <typename R>
-__global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
+__global__ void __launch_bounds__(256, 1) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
                                              const int* __restrict__ list, int* counter, int smem_bytes) {
   extern __shared__ __align__(256) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const SvdLayout L = svd_layout<R>(ws.D, (size_t)smem_bytes);
   int* hdr = reinterpret_cast<int*>(smem + L.hdr);
-  if (threadIdx.x == 0) hdr[HDR_TOT] = 0;
+  if (threadIdx.x == 0) { hdr[HDR_TOT] = 0; hdr[HDR_RTOT] = 0; }
   const int nbig = counter[1], total = counter[3];
   for (;;) {
     if (cl.block_rank() == 0 && threadIdx.x == 0) hdr[HDR_ITEM] = atomicAdd(&counter[0], 1);
@@ -1742,7 +1830,7 @@ __global__ void __launch_bounds__(256) k_svd(MpoDev st, SlotWS ws, const GateDes
     Slot sl = get_slot(ws, s);
     const GateDesc g = gates[s];
     const long long c0 = clock64();
-    big_block<R>(cl, st, sl, g, t, smem, L);
+    big_block<R>(cl, st, sl, g, t, smem, L, ws.cl_seed_max);
     if (st.ctr && threadIdx.x == 0 && cl.block_rank() == 0) {
       atomicAdd(st.ctr + CTR_CYC_BIG, (unsigned long long)(clock64() - c0));
       atomicAdd(st.ctr + CTR_NBIG, 1ull);
@@ -2071,7 +2159,22 @@ constexpr size_t SVD_SMEM = 200 * 1024;
 // k_svd cluster shape: K CTAs per cluster and the number of such clusters that fit on
 // the GPU at once (per precision), from cudaOccupancyMaxActiveClusters at start-up;
 // 0 clusters = launch without clusters (every large block then runs on one CTA).
-constexpr int SVD_CLUSTER = 8;
+// CTAs per cluster: 4, or GBS_MPO_SVD_CLUSTER_SIZE (1, 2, 4 or 8) from the environment.
+// Measured on GB300 (updates/s, K = 2 / 4 / 8): 16 modes FP64 5182 / 6131 / 5701, 32
+// modes chi 256 mixed 1187 / 1730 / 1434, 48 modes chi 512 mixed 291 / 476 / 350,
+// 64 instances mixed 71822 / 69018 / 60310.  36 clusters of 4 fit (144 CTAs).
+int svd_cluster_size() {
+  static int v = -1;
+  if (v < 0) {
+    v = 4;
+    const char* e = getenv("GBS_MPO_SVD_CLUSTER_SIZE");
+    if (e) {
+      const int k = atoi(e);
+      if (k == 1 || k == 2 || k == 4 || k == 8) v = k;
+    }
+  }
+  return v;
+}
 int g_svd_clusters[2] = {0, 0};
 
 // CTAs of the k_svd launch for a layer of nblk blocks (a multiple of the cluster size
@@ -2080,9 +2183,10 @@ template <typename R>
 int svd_grid(int nblk) {
   const int ncl = g_svd_clusters[sizeof(R) == 8 ? 0 : 1];
   if (ncl > 0) {
-    int want = (nblk + SVD_CLUSTER - 1) / SVD_CLUSTER;
+    const int K = svd_cluster_size();
+    int want = (nblk + K - 1) / K;
     if (want < 1) want = 1;
-    return (want < ncl ? want : ncl) * SVD_CLUSTER;
+    return (want < ncl ? want : ncl) * K;
   }
   const int sms = sm_count();
   return nblk < sms ? (nblk > 0 ? nblk : 1) : sms;
@@ -2099,7 +2203,7 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
   cfg.gridDim = dim3(grid);
   if (ncl > 0) {
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = SVD_CLUSTER;
+    at[0].val.clusterDim.x = svd_cluster_size();
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
@@ -2112,11 +2216,11 @@ template <typename R>
 int max_svd_clusters() {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  cfg.gridDim = dim3(SVD_CLUSTER * 64);
+  cfg.gridDim = dim3(svd_cluster_size() * 64);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = SVD_SMEM;
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = SVD_CLUSTER;
+  at[0].val.clusterDim.x = svd_cluster_size();
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -2191,8 +2295,21 @@ int svd_big_min() {
   return v;
 }
 
+// Largest Gram side of a cluster block that takes the single-CTA Gram seed: 64, or
+// GBS_MPO_SVD_CLUSTER_SEED_MAX (>= 0) from the environment (0 makes every cluster
+// block run the FP32 cluster phase; the tests use it).
+int svd_cluster_seed_max() {
+  static int v = -1;
+  if (v < 0) {
+    v = 64;
+    const char* e = getenv("GBS_MPO_SVD_CLUSTER_SEED_MAX");
+    if (e && atoi(e) >= 0) v = atoi(e);
+  }
+  return v;
+}
+
 int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32) {
-  if (cluster_size) *cluster_size = SVD_CLUSTER;
+  if (cluster_size) *cluster_size = svd_cluster_size();
   if (clusters_fp64) *clusters_fp64 = g_svd_clusters[0];
   if (clusters_fp32) *clusters_fp32 = g_svd_clusters[1];
   return 0;

@@ -55,7 +55,7 @@ struct MpoDev {
 
 // algorithmic work counters (real flops of the executed form)
 enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS,
-       CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_N };
+       CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_CYC_SEED, CTR_CYC_NS, CTR_CYC_POLISH, CTR_N };
 
 struct GateDesc {
   int inst, j, out, pad;
@@ -112,7 +112,8 @@ struct SlotWS {
   int* order;      // [S][capCand*2] candidate ids by rank (select)
   int* items;      // [S][P*P] contraction items a*P + b
   double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
-  int big_min;     // blocks with a Gram side >= big_min are factorised on a CTA cluster
+  int big_min;     // > 0: blocks with a Gram side >= big_min go to a CTA cluster (else the load rule)
+  int cl_seed_max; // cluster blocks with a Gram side <= this take the single-CTA Gram seed
   double2* NS;     // [S][capGram] Newton-Schulz scratch V^dag V of the FP64 refinement
   double2* VC;     // [S][capGram] refined right/left factors, column-major, path precision
                    // (never aliases the FP32 Gram or seed buffers of other blocks)

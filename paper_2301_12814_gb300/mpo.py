@@ -139,13 +139,15 @@ class Plan:
     def profile(self, with_jacobi: bool = False):
         """One instrumented replay: {stage: (ms, launches, flops)} (and, if asked,
         {blocks, two-sided sweeps, one-sided sweeps})."""
-        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(8)
+        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(11)
         _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl), _d(jb)), "mpo_plan_profile")
         out = {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
         if with_jacobi:
             return out, {"blocks": int(jb[0]), "sweeps": int(jb[1]), "refine_sweeps": int(jb[2]),
                          "seed_flops": float(jb[3]), "refine_flops": float(jb[4]), "cluster_blocks": int(jb[5]),
-                         "cluster_cycles": float(jb[6]), "cta_cycles": float(jb[7])}
+                         "cluster_cycles": float(jb[6]), "cta_cycles": float(jb[7]),
+                         "cluster_seed_cycles": float(jb[8]), "cluster_ns_cycles": float(jb[9]),
+                         "cluster_polish_cycles": float(jb[10])}
         return out
 
     def stage_times(self) -> dict:

@@ -1,9 +1,10 @@
 """The large-block SVD on a thread-block cluster, exercised on every block.
 
-By default only blocks with a Gram side of at least 48 go to a cluster, which the
-small parity workloads rarely reach.  Here a child process routes every block with a
-Gram side >= 1 through it (GBS_MPO_SVD_CLUSTER_MIN_N=1): many ragged column blocks,
-empty blocks, self-mirror blocks in the mirror-real basis.  The results must meet
+By default a block goes to a cluster only when it would be its layer's critical
+path, which the small parity workloads reach for a few blocks at most.  Here a child
+process routes every block with a Gram side >= 1 through it
+(GBS_MPO_SVD_CLUSTER_MIN_N=1): many ragged column blocks, empty blocks, self-mirror
+blocks in the mirror-real basis.  The results must meet
 the same bars as the single-CTA path against the FP64 oracle."""
 import json
 import os
@@ -17,12 +18,17 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-@pytest.fixture(scope="module")
-def results():
+@pytest.fixture(scope="module", params=["gram_seed", "fp32_phase"])
+def results(request):
+    """Every block on a cluster; cluster blocks of Gram side <= 64 seeded by the
+    single-CTA Gram eigensolver (the default), or all of them by the FP32 cluster
+    phase (GBS_MPO_SVD_CLUSTER_SEED_MAX=0)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     env = dict(os.environ, GBS_MPO_SVD_CLUSTER_MIN_N="1")
+    if request.param == "fp32_phase":
+        env["GBS_MPO_SVD_CLUSTER_SEED_MAX"] = "0"
     out = subprocess.run([sys.executable, os.path.join(HERE, "cluster_route_check.py")], env=env,
                          capture_output=True, text=True, timeout=1200)
     assert out.returncode == 0, out.stderr[-3000:]
