@@ -348,7 +348,10 @@ def run_native(args, ws, rank, local):
                    "seed_gflop_fp32": jac["seed_flops"] / 1e9, "refine_gflop": jac["refine_flops"] / 1e9,
                    "cluster_blocks": jac["cluster_blocks"],
                    "cluster_ms_per_block": jac["cluster_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6,
-                   "cta_ms_per_block": jac["cta_cycles"] / max(1, jac["blocks"] - jac["cluster_blocks"]) / 2.07e6,
+                   "cta_ms_per_block": jac["cta_cycles"] / max(1, jac["blocks"] - jac["cluster_blocks"]
+                                                                - jac["warp_blocks"]) / 2.07e6,
+                   "warp_blocks": jac["warp_blocks"],
+                   "warp_ms_per_block": jac["warp_cycles"] / max(1, jac["warp_blocks"]) / 2.07e6,
                    "cluster_ms_split": {k: jac[f"cluster_{k}_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6
                                         for k in ("seed", "ns", "polish")}},
         "wall_s": wall,

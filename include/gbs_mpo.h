@@ -134,12 +134,13 @@ int mpo_plan_launches(mpo_plan p);
  * seed Jacobi, per applied rotation 54 n (complex) or 18 n (real), plus the
  * refinement, W = Theta V and 48 h + 24 n per applied one-sided rotation, in the
  * path's precision; resplit: element copies).  Each array
- * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [11]): blocks
+ * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [13]): blocks
  * factorised, seed sweeps (two-sided, or the FP32 phase of a cluster block),
  * refinement sweeps, seed flops (FP32), refinement flops (path precision), blocks
  * factorised on a CTA cluster, SM clock cycles spent on cluster blocks (first CTA
- * of the cluster) and on single-CTA blocks, and the cluster blocks' cycles in their
- * seed (or FP32 phase), Newton-Schulz and final sweeps, summed over the replay.
+ * of the cluster) and on single-CTA blocks, the cluster blocks' cycles in their
+ * seed (or FP32 phase), Newton-Schulz and final sweeps, and the blocks factorised
+ * by one warp and their cycles, summed over the replay.
  * Same results as mpo_plan_run.  Synchronises. */
 mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
                             double* stage_flops, double* jacobi);

@@ -165,7 +165,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_ns = take((size_t)S * w.capGram * sizeof(double2));
   size_t o_vc = take((size_t)S * w.capGram * sizeof(double2));
   size_t o_ls = take((size_t)S * w.Pc * sizeof(int));
-  size_t o_ct = take(4 * sizeof(int));
+  size_t o_ct = take(8 * sizeof(int));
   void* buf = nullptr;
   CK(cudaMalloc(&buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
@@ -578,6 +578,8 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
     jacobi[8] = (double)ctr[CTR_CYC_SEED];
     jacobi[9] = (double)ctr[CTR_CYC_NS];
     jacobi[10] = (double)ctr[CTR_CYC_POLISH];
+    jacobi[11] = (double)ctr[CTR_NWARP];
+    jacobi[12] = (double)ctr[CTR_CYC_WARP];
   }
   return poll_error(h);
 }

@@ -1735,6 +1735,290 @@ __device__ void refine_block(const MpoDev& st, const Slot& sl, const GateDesc& g
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- small blocks on one warp
+// On the FP32 path a block of Gram side n <= 64 whose matrices fit in a slice of the
+// CTA's shared memory is factorised by a single warp, several blocks per CTA at a time,
+// with warp synchronisation only:
+//  * the FP32 Gram seed: two-sided parallel-order Jacobi on G (n x n, rows padded to
+//    n + 1), in the mirror-real basis for self-mirror blocks (real arithmetic): one
+//    lane per pair for the rotation parameters, lanes over rows / columns for the
+//    updates of each round;
+//  * W = Theta V (or Theta^dag V) and one-sided FP32 sweeps with one lane per column
+//    pair of a round, stopped as in the CTA refinement.
+// Slices: eight of 1/8 of the CTA's space for the smaller blocks, four of 1/4 for the
+// rest (a separate phase).  The results go where the CTA path puts them (sval, perm,
+// W, VC).
+constexpr int WARP_SVD_N = 64;
+constexpr int SVD_WARPS = 8;
+
+// A warp's slice: [header: rotation parameters of up to 32 pairs, the mirror map and
+// the column norms, 1280 B | seed A and V (padded rows), later W (n columns of stride
+// h | 1) | V (n columns of stride n | 1)].  The V offset clears both the seed and W;
+// the odd strides keep the lanes of the refinement, one per column pair, on distinct
+// shared-memory banks.
+constexpr size_t WARP_HDR_BYTES = 1280;
+__host__ __device__ __forceinline__ size_t warp_vc_offset(int n, int h) {
+  const size_t seed = 2ull * n * (n + 1) * sizeof(float2);
+  const size_t w = (size_t)(h + 1) * n * sizeof(float2);
+  return (seed > w ? seed : w);
+}
+__host__ __device__ __forceinline__ size_t warp_svd_bytes(int n, int h) {
+  return WARP_HDR_BYTES + warp_vc_offset(n, h) + (size_t)n * (n + 1) * sizeof(float2);
+}
+
+// header layout (byte offsets)
+constexpr int WH_CS = 0;      // 32 float2 (c, s)
+constexpr int WH_E = 256;     // 32 complex (or real) phases
+constexpr int WH_PQ = 512;    // 64 ints (p, q; q < 0: no rotation)
+constexpr int WH_MP = 768;    // 64 ints: mirror partner of each small-side index
+constexpr int WH_NRM = 1024;  // 64 floats: column norms^2
+
+template <typename E>
+__device__ int warp_jacobi(E* A, E* V, int n, int ld, unsigned char* hdr, int lane) {
+  const int np = n + (n & 1), half = np / 2;
+  float2* cs = reinterpret_cast<float2*>(hdr + WH_CS);
+  E* ph = reinterpret_cast<E*>(hdr + WH_E);
+  int* pq = reinterpret_cast<int*>(hdr + WH_PQ);
+  for (int i = lane; i < n; i += 32)
+    for (int j = 0; j < n; ++j) V[i * ld + j] = (i == j) ? unit_e<E>() : zero_e<E>();
+  float dm = 0.f;
+  for (int i = 0; i < n; ++i) dm = fmaxf(dm, absv(re(A[i * ld + i])));
+  const float tol_abs = Prec<float>::tol_abs * dm, tol_rel = Prec<float>::tol_rel;
+  int sweep = 0;
+  __syncwarp();
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    bool any = false;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      if (lane < half) {
+        int p, q;
+        circle_pair(rnd, lane, np, p, q);
+        int qq = -1;
+        float c = 1.f, s = 0.f;
+        E e = unit_e<E>();
+        if (q < n) {
+          const float a = re(A[p * ld + p]), b = re(A[q * ld + q]);
+          const E gpq = A[p * ld + q];
+          const float hh = absv(gpq);
+          if (hh > tol_rel * sqrtf(fabsf(a * b)) && hh > tol_abs) {
+            const float tau = (b - a) / (2.f * hh);
+            const float tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + tt * tt);
+            s = tt * c;
+            e = divr<E, float>(gpq, hh);
+            qq = q;
+          }
+        }
+        pq[2 * lane] = p;
+        pq[2 * lane + 1] = qq;
+        cs[lane] = make_float2(c, s);
+        ph[lane] = e;
+        any = any || (qq >= 0);
+      }
+      __syncwarp();
+      for (int k = 0; k < half; ++k) {
+        const int q = pq[2 * k + 1];
+        if (q < 0) continue;
+        const int p = pq[2 * k];
+        const float c = cs[k].x, s = cs[k].y;
+        const E ec = cj(ph[k]);
+        for (int i = lane; i < n; i += 32) {  // columns p, q of A and V
+          const E x = A[i * ld + p], ys = mulv(A[i * ld + q], ec);
+          A[i * ld + p] = lin(c, x, -s, ys);
+          A[i * ld + q] = lin(s, x, c, ys);
+          const E vx = V[i * ld + p], vys = mulv(V[i * ld + q], ec);
+          V[i * ld + p] = lin(c, vx, -s, vys);
+          V[i * ld + q] = lin(s, vx, c, vys);
+        }
+      }
+      __syncwarp();
+      for (int k = 0; k < half; ++k) {
+        const int q = pq[2 * k + 1];
+        if (q < 0) continue;
+        const int p = pq[2 * k];
+        const float c = cs[k].x, s = cs[k].y;
+        const E e = ph[k];
+        for (int i = lane; i < n; i += 32) {  // rows p, q of A
+          const E x = A[p * ld + i], ye = mulv(e, A[q * ld + i]);
+          A[p * ld + i] = lin(c, x, -s, ye);
+          A[q * ld + i] = lin(s, x, c, ye);
+        }
+      }
+      __syncwarp();
+    }
+    if (!__any_sync(0xffffffffu, any)) break;
+  }
+  return sweep;
+}
+
+// One block on one warp (FP32 path).  slice: this warp's shared-memory slice.
+__device__ void warp_block(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, unsigned char* slice,
+                           int lane) {
+  typedef float2 C;
+  const int n = sl.f(BF_G, t), r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
+  const int h = side == 0 ? c : r;
+  const int ncap = st.ncap, P = st.P, M = st.M;
+  const bool selfm = pair_mirror(sl.f(BF_M, t), ncap) == sl.f(BF_M, t);
+  const int ld = n + 1;
+  unsigned char* hdr = slice;
+  int* mp = reinterpret_cast<int*>(hdr + WH_MP);
+  float* nrm = reinterpret_cast<float*>(hdr + WH_NRM);
+  unsigned char* data = slice + WARP_HDR_BYTES;
+  const C* gG = reinterpret_cast<const C*>(sl.G) + sl.f(BF_GOFF, t);
+  const C* Th = reinterpret_cast<const C*>(sl.theta) + sl.f(BF_TOFF, t);
+  C* Vc = reinterpret_cast<C*>(data + warp_vc_offset(n, h));  // V for the refinement
+  const int ldv = n | 1, ldw = h | 1;  // odd strides (<= n + 1, h + 1: within the slice layout)
+  const float hs = 0.70710678118654752440f;
+  for (int i = lane; i < n; i += 32) mp[i] = i;
+  if (selfm) {
+    const long long bX = (long long)g.inst * (M + 1) + g.j + (side == 0 ? 0 : 2);
+    for (int i = lane; i < n; i += 32) mp[i] = mirror_coord(sl, st, g, t, side, i, st.segoff + bX * (P + 1));
+  }
+  __syncwarp();
+  // column k of the mirror-real basis B: e_k (k its own mirror), (e_k + e_p)/sqrt2 (k < p),
+  // i (e_p - e_k)/sqrt2 (k > p), p the mirror of k
+  auto basis = [&](int k, int* idx, C* wt) {
+    const int p = mp[k];
+    if (p == k) { idx[0] = k; wt[0] = make_float2(1.f, 0.f); return 1; }
+    if (k < p) { idx[0] = k; wt[0] = make_float2(hs, 0.f); idx[1] = p; wt[1] = make_float2(hs, 0.f); return 2; }
+    idx[0] = p; wt[0] = make_float2(0.f, hs); idx[1] = k; wt[1] = make_float2(0.f, -hs); return 2;
+  };
+  int sweeps;
+  if (selfm) {
+    float* A = reinterpret_cast<float*>(data);
+    float* V = A + n * ld;
+    for (int e = lane; e < n * n; e += 32) {  // A[i][j] = Re(b_i^dag G b_j)
+      const int i = e / n, j = e % n;
+      int ia[2], jb[2];
+      C wa[2], wb[2];
+      const int na = basis(i, ia, wa), nb = basis(j, jb, wb);
+      float acc = 0.f;
+      for (int x = 0; x < na; ++x)
+        for (int y = 0; y < nb; ++y) acc += cmul(cmul(cj(wa[x]), gG[(long long)ia[x] * n + jb[y]]), wb[y]).x;
+      A[i * ld + j] = acc;
+    }
+    __syncwarp();
+    sweeps = warp_jacobi<float>(A, V, n, ld, hdr, lane);
+    for (int e = lane; e < n * n; e += 32) {  // V = B V~, column-major
+      const int k = e / n, i = e % n, pi = mp[i];
+      C out;
+      if (pi == i) out = make_float2(V[i * ld + k], 0.f);
+      else if (i < pi) out = make_float2(hs * V[i * ld + k], hs * V[pi * ld + k]);
+      else out = make_float2(hs * V[pi * ld + k], -hs * V[i * ld + k]);
+      Vc[(size_t)k * ldv + i] = out;
+    }
+  } else {
+    C* A = reinterpret_cast<C*>(data);
+    C* V = A + n * ld;
+    for (int e = lane; e < n * n; e += 32) A[(e / n) * ld + e % n] = gG[e];
+    __syncwarp();
+    sweeps = warp_jacobi<C>(A, V, n, ld, hdr, lane);
+    for (int e = lane; e < n * n; e += 32) Vc[(size_t)(e / n) * ldv + e % n] = V[(e % n) * ld + e / n];
+  }
+  __syncwarp();
+  if (st.ctr && lane == 0) {
+    atomicAdd(st.ctr + CTR_SWEEPS, (unsigned long long)(sweeps + 1));
+    atomicAdd(st.ctr + CTR_EIGBLK, 1ull);
+  }
+  // W = Theta V (side 1) or Theta^dag V (side 0), at the slice data start
+  C* W = reinterpret_cast<C*>(data);
+  for (long long e = lane; e < (long long)h * n; e += 32) {
+    const int k = (int)(e / h), x = (int)(e % h);
+    C acc = zero_e<C>();
+    if (side == 1) {
+      for (int q = 0; q < n; ++q) cfma(acc, Th[(long long)x * c + q], Vc[(size_t)k * ldv + q]);
+    } else {
+      for (int i = 0; i < n; ++i) cfma_cj(acc, Th[(long long)i * c + x], Vc[(size_t)k * ldv + i]);
+    }
+    W[(size_t)k * ldw + x] = acc;
+  }
+  __syncwarp();
+  auto col_norms = [&]() {
+    for (int k = lane; k < n; k += 32) {
+      float a = 0.f;
+      for (int x = 0; x < h; ++x) { const C w = W[(size_t)k * ldw + x]; a += w.x * w.x + w.y * w.y; }
+      nrm[k] = a;
+    }
+    __syncwarp();
+  };
+  col_norms();
+  float mx = 0.f;
+  for (int k = 0; k < n; ++k) mx = fmaxf(mx, nrm[k]);
+  const float tol_abs = (float)Prec<float>::os_abs * mx, col_floor = (float)(Prec<float>::floor * mx);
+  // one-sided sweeps, one lane per column pair of the round
+  const int np = n + (n & 1), half = np / 2;
+  int rs = 0;
+  unsigned long long nrot = 0;
+  for (; rs < JACOBI_MAX_SWEEPS; ++rs) {
+    bool any = false;
+    float wr2 = 0.f;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      if (lane < half) {
+        int p, q;
+        circle_pair(rnd, lane, np, p, q);
+        if (q < n) {
+          C* wp = W + (size_t)p * ldw;
+          C* wq = W + (size_t)q * ldw;
+          float al = 0.f, be = 0.f;
+          C ga = zero_e<C>();
+          for (int x = 0; x < h; ++x) {
+            const C a = wp[x], b = wq[x];
+            al += a.x * a.x + a.y * a.y;
+            be += b.x * b.x + b.y * b.y;
+            cfma_cj(ga, a, b);
+          }
+          if (al > col_floor && be > col_floor)
+            wr2 = fmaxf(wr2, rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y));
+          float cs_, sn;
+          C e;
+          if (os_params(al, be, ga, selfm, tol_abs, col_floor, cs_, sn, e)) {
+            const C ec = cj(e);
+            for (int x = 0; x < h; ++x) {
+              const C a = wp[x], bs = mulv(wq[x], ec);
+              wp[x] = lin(cs_, a, -sn, bs);
+              wq[x] = lin(sn, a, cs_, bs);
+            }
+            C* vp = Vc + (size_t)p * ldv;
+            C* vq = Vc + (size_t)q * ldv;
+            for (int x = 0; x < n; ++x) {
+              const C a = vp[x], bs = mulv(vq[x], ec);
+              vp[x] = lin(cs_, a, -sn, bs);
+              vq[x] = lin(sn, a, cs_, bs);
+            }
+            any = true;
+            ++nrot;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    any = __any_sync(0xffffffffu, any);
+    for (int o = 16; o > 0; o >>= 1) wr2 = fmaxf(wr2, __shfl_xor_sync(0xffffffffu, wr2, o));
+    if (!any) break;
+    if ((double)wr2 < Prec<float>::stop2) { ++rs; break; }
+  }
+  for (int o = 16; o > 0; o >>= 1) nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+  // singular values = column norms, ranked descending (ties by index)
+  col_norms();
+  const int coff = sl.f(BF_COFF, t);
+  for (int i = lane; i < n; i += 32) {
+    const float wi = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite(wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4700 + t);
+    sl.sval[coff + rank] = sqrt((double)wi);
+    sl.perm[coff + rank] = i;
+  }
+  C* gW = reinterpret_cast<C*>(sl.W) + sl.f(BF_TOFF, t);
+  C* gVc = reinterpret_cast<C*>(sl.VC) + sl.f(BF_GOFF, t);
+  for (long long e = lane; e < (long long)h * n; e += 32) gW[e] = W[(size_t)(e / h) * ldw + e % h];
+  for (int e = lane; e < n * n; e += 32) gVc[e] = Vc[(size_t)(e / n) * ldv + e % n];
+  if (st.ctr && lane == 0) {
+    atomicAdd(st.ctr + CTR_REFINE, nrot * (48ull * h + 24ull * n) + 8ull * (unsigned long long)h * n * n);
+    atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(rs + 1));
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- k_order, k_svd
 // The blocks of all gates of a layer go into one list: the large ones first, then the
 // rest, each part longest first (bucketed by log2 of an n^2 (n + h) work estimate),
@@ -1751,17 +2035,22 @@ __device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int mi
   return n >= min_n && (n > seed_max || svd_work(n, h) * (unsigned long long)ncta > total);
 }
 
-__device__ __forceinline__ int order_key(bool big, int n, int h) {
-  return (big ? 0 : 64) + 63 - min(63, (int)log2((double)svd_work(n, h) + 1.0));
+// category: 0 cluster, 1 one CTA, 2 one warp in a quarter slice, 3 one warp in an
+// eighth slice
+__device__ __forceinline__ int order_key(int cat, int n, int h) {
+  return cat * 64 + 63 - min(63, (int)log2((double)svd_work(n, h) + 1.0));
 }
 
-// ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block.
+// ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block;
+// room: the shared memory a CTA has for block data on the FP32 path (0: the FP64 path,
+// no warp blocks).  counter: cursor and end of the cluster ([0], [1]), CTA ([2], [3]),
+// quarter-slice warp ([4], [5]) and eighth-slice warp ([6], [7]) parts of list.
 __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter, int ncta,
-                                                int min_n, int seed_max) {
-  __shared__ int hist[128], start[128];
+                                                int min_n, int seed_max, int room) {
+  __shared__ int hist[256], start[256];
   __shared__ unsigned long long total;
   const int tid = threadIdx.x, Pc = ws.Pc, E = ngates * Pc;
-  if (tid < 128) hist[tid] = 0;
+  if (tid < 256) hist[tid] = 0;
   if (tid == 0) total = 0;
   __syncthreads();
   for (int e = tid; e < E; e += blockDim.x) {
@@ -1773,24 +2062,36 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
   }
   __syncthreads();
   const unsigned long long tot = total;
+  const size_t eighth = (((size_t)room / SVD_WARPS) & ~(size_t)15), quarter = (((size_t)room / 4) & ~(size_t)15);
+  auto category = [&](int n, int h) {
+    if (route_big(ws, n, h, min_n, seed_max, tot, ncta)) return 0;
+    // a block on the layer's critical path keeps a whole CTA (lower latency than one warp)
+    const bool critical = svd_work(n, h) * (unsigned long long)ncta > tot;
+    if (room > 0 && n <= WARP_SVD_N && !critical) {
+      const size_t b = warp_svd_bytes(n, h);
+      if (b <= eighth) return 3;
+      if (b <= quarter) return 2;
+    }
+    return 1;
+  };
   for (int e = tid; e < E; e += blockDim.x) {
     Slot sl = get_slot(ws, e / Pc);
     const int t = e % Pc;
     const int n = sl.f(BF_G, t);
     if (sl.scal[SS_STATUS] || n == 0) continue;
     const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    atomicAdd(&hist[order_key(route_big(ws, n, h, min_n, seed_max, tot, ncta), n, h)], 1);
+    atomicAdd(&hist[order_key(category(n, h), n, h)], 1);
   }
   __syncthreads();
   if (tid == 0) {
     int acc = 0;
-    for (int k = 0; k < 128; ++k) {
-      if (k == 64) { counter[1] = acc; counter[2] = acc; }
+    for (int k = 0; k < 256; ++k) {
+      if (k % 64 == 0 && k > 0) { counter[2 * (k / 64) - 1] = acc; counter[2 * (k / 64)] = acc; }
       start[k] = acc;
       acc += hist[k];
     }
     counter[0] = 0;
-    counter[3] = acc;
+    counter[7] = acc;
   }
   __syncthreads();
   for (int e = tid; e < E; e += blockDim.x) {
@@ -1799,7 +2100,7 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
     const int n = sl.f(BF_G, t);
     if (sl.scal[SS_STATUS] || n == 0) continue;
     const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    list[atomicAdd(&start[order_key(route_big(ws, n, h, min_n, seed_max, tot, ncta), n, h)], 1)] = e;
+    list[atomicAdd(&start[order_key(category(n, h), n, h)], 1)] = e;
   }
 }
 
@@ -1817,7 +2118,7 @@ __global__ void __launch_bounds__(256, 1) k_svd(MpoDev st, SlotWS ws, const Gate
   const SvdLayout L = svd_layout<R>(ws.D, (size_t)smem_bytes);
   int* hdr = reinterpret_cast<int*>(smem + L.hdr);
   if (threadIdx.x == 0) { hdr[HDR_TOT] = 0; hdr[HDR_RTOT] = 0; }
-  const int nbig = counter[1], total = counter[3];
+  const int nbig = counter[1], ncta_end = counter[3], nwide_end = counter[5], total = counter[7];
   for (;;) {
     if (cl.block_rank() == 0 && threadIdx.x == 0) hdr[HDR_ITEM] = atomicAdd(&counter[0], 1);
     cl.sync();
@@ -1841,7 +2142,7 @@ __global__ void __launch_bounds__(256, 1) k_svd(MpoDev st, SlotWS ws, const Gate
     __syncthreads();
     const int idx = hdr[HDR_ITEM];
     __syncthreads();
-    if (idx >= total) break;
+    if (idx >= ncta_end) break;
     const int e = list[idx];
     const int s = e / ws.Pc, t = e % ws.Pc;
     Slot sl = get_slot(ws, s);
@@ -1855,6 +2156,35 @@ __global__ void __launch_bounds__(256, 1) k_svd(MpoDev st, SlotWS ws, const Gate
     if (seeded) seed_block(st, sl, g, t, smem, L);
     refine_block<R>(st, sl, g, t, smem, L, seeded);
     if (st.ctr && threadIdx.x == 0) atomicAdd(st.ctr + CTR_CYC_SMALL, (unsigned long long)(clock64() - c0));
+  }
+  // small blocks on the FP32 path: one warp each, in a quarter (warps 0-3) and then
+  // an eighth (all warps) of the shared memory
+  if (sizeof(R) == 4 && total > ncta_end) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto warp_phase = [&](int* cursor, int end, int nslices) {
+      const size_t slice_bytes = ((L.total - L.data) / nslices) & ~(size_t)15;
+      if (warp >= nslices) return;
+      unsigned char* slice = smem + L.data + warp * slice_bytes;
+      for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(cursor, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= end) break;
+        const int e = list[idx];
+        const int s = e / ws.Pc, t = e % ws.Pc;
+        Slot sl = get_slot(ws, s);
+        const GateDesc g = gates[s];
+        const long long c0 = clock64();
+        warp_block(st, sl, g, t, slice, lane);
+        if (st.ctr && lane == 0) {
+          atomicAdd(st.ctr + CTR_CYC_WARP, (unsigned long long)(clock64() - c0));
+          atomicAdd(st.ctr + CTR_NWARP, 1ull);
+        }
+      }
+    };
+    warp_phase(&counter[4], nwide_end, 4);
+    __syncthreads();  // the quarter slices overlap the eighth slices
+    warp_phase(&counter[6], total, SVD_WARPS);
   }
 }
 
@@ -2252,7 +2582,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   const int svd_ctas = svd_grid<R>(nblk);
   const SvdLayout SL = svd_layout<R>(ws.D, SVD_SMEM);
   const int seed_max = (int)sqrt((double)(SL.total - SL.data) / (2.0 * sizeof(float2)));
-  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max);
+  const int room = sizeof(R) == 4 ? (int)(SL.total - SL.data) : 0;
+  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max, room);
   if (ev) record_stage_event(ev[4], st);
   launch_svd<R>(s, ws, d_gates, svd_ctas, st);
   if (ev) record_stage_event(ev[5], st);

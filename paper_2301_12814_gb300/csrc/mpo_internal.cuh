@@ -55,7 +55,8 @@ struct MpoDev {
 
 // algorithmic work counters (real flops of the executed form)
 enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS,
-       CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_CYC_SEED, CTR_CYC_NS, CTR_CYC_POLISH, CTR_N };
+       CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_CYC_SEED, CTR_CYC_NS, CTR_CYC_POLISH, CTR_NWARP,
+       CTR_CYC_WARP, CTR_N };
 
 struct GateDesc {
   int inst, j, out, pad;
@@ -118,7 +119,7 @@ struct SlotWS {
   double2* VC;     // [S][capGram] refined right/left factors, column-major, path precision
                    // (never aliases the FP32 Gram or seed buffers of other blocks)
   int* list;       // [S * Pc] layer's blocks, longest first (k_order)
-  int* counter;    // [4]: next large item, large items, next small item, all items
+  int* counter;    // [8]: cursors and ends of the cluster, CTA and warp parts of list (k_order)
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }

@@ -139,7 +139,7 @@ class Plan:
     def profile(self, with_jacobi: bool = False):
         """One instrumented replay: {stage: (ms, launches, flops)} (and, if asked,
         {blocks, two-sided sweeps, one-sided sweeps})."""
-        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(11)
+        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(13)
         _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl), _d(jb)), "mpo_plan_profile")
         out = {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
         if with_jacobi:
@@ -147,7 +147,8 @@ class Plan:
                          "seed_flops": float(jb[3]), "refine_flops": float(jb[4]), "cluster_blocks": int(jb[5]),
                          "cluster_cycles": float(jb[6]), "cta_cycles": float(jb[7]),
                          "cluster_seed_cycles": float(jb[8]), "cluster_ns_cycles": float(jb[9]),
-                         "cluster_polish_cycles": float(jb[10])}
+                         "cluster_polish_cycles": float(jb[10]), "warp_blocks": int(jb[11]),
+                         "warp_cycles": float(jb[12])}
         return out
 
     def stage_times(self) -> dict:
