@@ -71,11 +71,16 @@ template <typename R> struct Prec;
 // W = Theta V; floor: singular values with s^2 <= floor * s_max^2 are dropped (the
 // refined values are accurate to a few ulps of s_max, not of s_max^2).
 // stop2: once the largest relative off-diagonal |w_p^dag w_q|^2 / (|w_p|^2 |w_q|^2) of a
-// one-sided sweep is below stop2, the quadratically convergent next sweep could only
-// apply rotations below the tolerance, so the iteration stops after this sweep.
+// one-sided sweep is below stop2, the iteration stops after this sweep: it leaves
+// off-diagonals of order stop2 (quadratic convergence), which perturb the singular
+// values at second order and the vectors at first order.  FP64: 1e-12 (vectors to
+// ~1e-12, two orders inside the 1e-10 parity bar; the whole 32-mode chi = 256 mesh
+// meets the oracle to 1.2e-12 with it); FP32: 1e-10.  The criterion covers every
+// pair above the column floor: a small kept column still matters, because the
+// re-split divides by the neighbouring bonds' lambda.
 template <> struct Prec<double> {
   typedef double2 C;
-  static constexpr double stop2 = 1e-16;
+  static constexpr double stop2 = 1e-12;
   static constexpr double tol_rel = 1e-15, tol_abs = 1e-18;
   static constexpr double os_rel = 4e-15, os_abs = 1e-30;
   static constexpr double floor = 1e-28;
@@ -2049,16 +2054,28 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
                                                 int min_n, int seed_max, int room) {
   __shared__ int hist[256], start[256];
   __shared__ unsigned long long total;
-  const int tid = threadIdx.x, Pc = ws.Pc, E = ngates * Pc;
+  const int tid = threadIdx.x, lane = tid & 31, Pc = ws.Pc, E = ngates * Pc;
   if (tid < 256) hist[tid] = 0;
   if (tid == 0) total = 0;
   __syncthreads();
-  for (int e = tid; e < E; e += blockDim.x) {
+  // every warp walks whole rounds of 32 entries so that the warp-level reductions and
+  // key matching below always run with all lanes (entries past E are invalid)
+  const int Er = (E + 31) & ~31;
+  auto entry = [&](int e, int& n, int& h) {
+    n = 0; h = 0;
+    if (e >= E) return;
     Slot sl = get_slot(ws, e / Pc);
     const int t = e % Pc;
-    const int n = sl.f(BF_G, t);
-    if (sl.scal[SS_STATUS] || n == 0) continue;
-    atomicAdd(&total, svd_work(n, sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t)));
+    if (sl.scal[SS_STATUS]) return;
+    n = sl.f(BF_G, t);
+    h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
+  };
+  for (int e = tid; e < Er; e += blockDim.x) {
+    int n, h;
+    entry(e, n, h);
+    unsigned long long w = n > 0 ? svd_work(n, h) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0 && w) atomicAdd(&total, w);
   }
   __syncthreads();
   const unsigned long long tot = total;
@@ -2074,13 +2091,16 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
     }
     return 1;
   };
-  for (int e = tid; e < E; e += blockDim.x) {
-    Slot sl = get_slot(ws, e / Pc);
-    const int t = e % Pc;
-    const int n = sl.f(BF_G, t);
-    if (sl.scal[SS_STATUS] || n == 0) continue;
-    const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    atomicAdd(&hist[order_key(category(n, h), n, h)], 1);
+  // warp-aggregated atomics: one per distinct key in the warp (keys cluster heavily)
+  auto key_of = [&](int e) {
+    int n, h;
+    entry(e, n, h);
+    return n > 0 ? order_key(category(n, h), n, h) : -1;
+  };
+  for (int e = tid; e < Er; e += blockDim.x) {
+    const int key = key_of(e);
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(&hist[key], __popc(grp));
   }
   __syncthreads();
   if (tid == 0) {
@@ -2094,13 +2114,14 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
     counter[7] = acc;
   }
   __syncthreads();
-  for (int e = tid; e < E; e += blockDim.x) {
-    Slot sl = get_slot(ws, e / Pc);
-    const int t = e % Pc;
-    const int n = sl.f(BF_G, t);
-    if (sl.scal[SS_STATUS] || n == 0) continue;
-    const int h = sl.f(BF_SIDE, t) == 0 ? sl.f(BF_C, t) : sl.f(BF_R, t);
-    list[atomicAdd(&start[order_key(category(n, h), n, h)], 1)] = e;
+  for (int e = tid; e < Er; e += blockDim.x) {
+    const int key = key_of(e);
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (key >= 0 && lane == leader) base = atomicAdd(&start[key], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (key >= 0) list[base + __popc(grp & ((1u << lane) - 1u))] = e;
   }
 }
 
