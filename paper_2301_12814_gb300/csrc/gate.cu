@@ -219,20 +219,25 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
   const double ct = cos(g.theta), sn = sin(g.theta), cp = cos(g.phi), spp = sin(g.phi);
   const double2 S11 = make_double2(cp * ct, spp * ct), S21 = make_double2(cp * sn, spp * sn);
   const double2 S12 = make_double2(-sn, 0.0), S22 = make_double2(ct, 0.0);
+  // sqrt(k) and 1/sqrt(k) for k <= ncap, once per CTA (FP64 square roots and divisions
+  // are long instruction sequences on this part; the recurrence below only looks them up)
+  __shared__ double sqt[MPO_NCAP_MAX + 2], isqt[MPO_NCAP_MAX + 2];
+  if (tid <= ncap + 1) {
+    sqt[tid] = sqrt((double)tid);
+    isqt[tid] = tid > 0 ? 1.0 / sqt[tid] : 0.0;
+  }
   if (tid == 0) fk[0] = make_double2(1.0, 0.0);
   __syncthreads();
   for (int n = 1; n <= ncap; ++n) {
     const int o1 = fock_off(n - 1), o = fock_off(n);
-    for (int jj = tid; jj <= n; jj += nth) {
+    for (int e = tid; e < (n + 1) * (n + 1); e += nth) {
+      const int jj = e % (n + 1), i = e / (n + 1);
       const int src = (jj >= 1) ? jj - 1 : 0;
       const double2 al = (jj >= 1) ? S11 : S12, be = (jj >= 1) ? S21 : S22;
-      const double sc = 1.0 / sqrt((double)((jj >= 1) ? jj : n));
-      for (int i = 0; i <= n; ++i) {
-        double2 acc = make_double2(0.0, 0.0);
-        if (i >= 1) cfma(acc, cscale(al, sqrt((double)i)), fk[o1 + (i - 1) * n + src]);
-        if (i <= n - 1) cfma(acc, cscale(be, sqrt((double)(n - i))), fk[o1 + i * n + src]);
-        fk[o + i * (n + 1) + jj] = cscale(acc, sc);
-      }
+      double2 acc = make_double2(0.0, 0.0);
+      if (i >= 1) cfma(acc, cscale(al, sqt[i]), fk[o1 + (i - 1) * n + src]);
+      if (i <= n - 1) cfma(acc, cscale(be, sqt[n - i]), fk[o1 + i * n + src]);
+      fk[o + i * (n + 1) + jj] = cscale(acc, isqt[(jj >= 1) ? jj : n]);
     }
     __syncthreads();
   }
@@ -254,35 +259,56 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
       }
   }
   __syncthreads();
-  // per canonical block: rows, cols, non-empty test, segment offsets
-  for (int t = tid; t < Pc; t += nth) {
-    const int m = canon_pair(t, ncap), cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
-    int r = 0, c = 0;
-    for (int a = 0; a < P; ++a) {
-      int na = segA[a + 1] - segA[a];
-      if (na > 0 && pair_c(a, ncap) >= cm && pair_cb(a, ncap) >= cbm) {
-        sl.rowoff[t * P + a] = r; r += na;
-      } else sl.rowoff[t * P + a] = -1;
-      int nb = segB[a + 1] - segB[a];
-      if (nb > 0 && pair_c(a, ncap) <= cm && pair_cb(a, ncap) <= cbm) {
-        sl.coloff[t * P + a] = c; c += nb;
-      } else sl.coloff[t * P + a] = -1;
+  // per canonical block (one warp each): rows, cols, non-empty test, segment offsets.
+  // The row (column) offset of pair a is the running sum of the sizes of the earlier
+  // pairs a' >= m (<= m): an inclusive warp scan per group of 32 pairs plus a carry.
+  {
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    for (int t = warp; t < Pc; t += nwarp) {
+      const int m = canon_pair(t, ncap), cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
+      int r = 0, c = 0;
+      for (int a0 = 0; a0 < P; a0 += 32) {
+        const int a = a0 + lane;
+        int na = 0, nb = 0;
+        if (a < P) {
+          const int ca = pair_c(a, ncap), cba = pair_cb(a, ncap);
+          if (ca >= cm && cba >= cbm) na = segA[a + 1] - segA[a];
+          if (ca <= cm && cba <= cbm) nb = segB[a + 1] - segB[a];
+        }
+        int sa = na, sb = nb;  // inclusive scans
+        for (int o = 1; o < 32; o <<= 1) {
+          const int ua = __shfl_up_sync(0xffffffffu, sa, o), ub = __shfl_up_sync(0xffffffffu, sb, o);
+          if (lane >= o) { sa += ua; sb += ub; }
+        }
+        if (a < P) {
+          sl.rowoff[t * P + a] = na > 0 ? r + sa - na : -1;
+          sl.coloff[t * P + a] = nb > 0 ? c + sb - nb : -1;
+        }
+        r += __shfl_sync(0xffffffffu, sa, 31);
+        c += __shfl_sync(0xffffffffu, sb, 31);
+      }
+      // non-empty: some present c, a >= max(c, m), b <= min(c, m)
+      bool path = false;
+      for (int c0 = 0; c0 < P && !path; c0 += 32) {
+        const int cc = c0 + lane;
+        bool ok = false;
+        if (cc < P && segC[cc + 1] > segC[cc]) {
+          const int x = pair_c(cc, ncap), y = pair_cb(cc, ncap);
+          const int hx = x > cm ? x : cm, hy = y > cbm ? y : cbm;
+          const int lx = x < cm ? x : cm, ly = y < cbm ? y : cbm;
+          ok = box_count(preA, q, hx, ncap, hy, ncap) > 0 && box_count(preB, q, 0, lx, 0, ly) > 0;
+        }
+        path = __any_sync(0xffffffffu, ok);
+      }
+      if (lane == 0) {
+        const int gg = (r > 0 && c > 0 && path) ? (r < c ? r : c) : 0;
+        sl.f(BF_M, t) = m;
+        sl.f(BF_R, t) = gg ? r : 0;
+        sl.f(BF_C, t) = gg ? c : 0;
+        sl.f(BF_G, t) = gg;
+        sl.f(BF_SIDE, t) = (r <= c) ? 0 : 1;
+      }
     }
-    // non-empty: some present c, a >= max(c, m), b <= min(c, m)
-    bool path = false;
-    for (int cc = 0; cc < P && !path; ++cc) {
-      if (segC[cc + 1] == segC[cc]) continue;
-      int x = pair_c(cc, ncap), y = pair_cb(cc, ncap);
-      int hx = x > cm ? x : cm, hy = y > cbm ? y : cbm;
-      int lx = x < cm ? x : cm, ly = y < cbm ? y : cbm;
-      if (box_count(preA, q, hx, ncap, hy, ncap) > 0 && box_count(preB, q, 0, lx, 0, ly) > 0) path = true;
-    }
-    const int gg = (r > 0 && c > 0 && path) ? (r < c ? r : c) : 0;
-    sl.f(BF_M, t) = m;
-    sl.f(BF_R, t) = gg ? r : 0;
-    sl.f(BF_C, t) = gg ? c : 0;
-    sl.f(BF_G, t) = gg;
-    sl.f(BF_SIDE, t) = (r <= c) ? 0 : 1;
   }
   __syncthreads();
   // occupancy of non-empty canonical blocks for the item test; offsets and capacities
@@ -358,16 +384,20 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
       if (box_count(preM, q, cb, ca, cbb, cba) > 0) sl.items[o++] = a * P + b;
     }
   }
-  // row / column maps: Theta(m) row i -> bond A index, column -> bond B index
-  for (int t = tid; t < Pc; t += nth) {
-    if (sl.f(BF_G, t) == 0) continue;
-    int* rmap = sl.rowmap + sl.f(BF_RMOFF, t);
-    int* cmap = sl.colmap + sl.f(BF_CMOFF, t);
-    for (int a = 0; a < P; ++a) {
-      int o = sl.rowoff[t * P + a];
-      if (o >= 0) for (int i = segA[a]; i < segA[a + 1]; ++i) rmap[o + i - segA[a]] = i;
-      int oc = sl.coloff[t * P + a];
-      if (oc >= 0) for (int i = segB[a]; i < segB[a + 1]; ++i) cmap[oc + i - segB[a]] = i;
+  // row / column maps: Theta(m) row i -> bond A index, column -> bond B index (one warp
+  // per block, lanes over pairs)
+  {
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    for (int t = warp; t < Pc; t += nwarp) {
+      if (sl.f(BF_G, t) == 0) continue;
+      int* rmap = sl.rowmap + sl.f(BF_RMOFF, t);
+      int* cmap = sl.colmap + sl.f(BF_CMOFF, t);
+      for (int a = lane; a < P; a += 32) {
+        const int o = sl.rowoff[t * P + a];
+        if (o >= 0) for (int i = segA[a]; i < segA[a + 1]; ++i) rmap[o + i - segA[a]] = i;
+        const int oc = sl.coloff[t * P + a];
+        if (oc >= 0) for (int i = segB[a]; i < segB[a + 1]; ++i) cmap[oc + i - segB[a]] = i;
+      }
     }
   }
 }
@@ -2225,6 +2255,8 @@ __device__ double block_sum(double v, double* red) {
 
 // count of entries of a descending list that precede key (s, m, k) in the order
 // (s desc, m asc, k asc); the list has pair index ml and alive length len.
+constexpr int SELECT_STAGE = 3072;  // alive singular values k_select stages in shared memory
+
 __device__ __forceinline__ int count_before(const double* lst, int len, int ml, double sv, int m, int k) {
   if (ml == m) return k;
   int lo = 0, hi = len;
@@ -2249,17 +2281,20 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
   __shared__ int newseg[MPO_P_MAX + 1];
   __shared__ int keep_sh, nalive_sh;
   const int NL = 2 * Pc;
-  // 1. s_max and total weight
+  // 1. s_max and total weight: one thread per candidate value (the blocks' value lists
+  // are contiguous in candidate order; a non-self-mirror block's values count twice)
+  __shared__ int coffs[MPO_PC_MAX + 1];
+  __shared__ unsigned char cmult[MPO_PC_MAX];
+  for (int t = tid; t <= Pc; t += nth) {
+    coffs[t] = sl.f(BF_COFF, t);
+    if (t < Pc) cmult[t] = pair_mirror(sl.f(BF_M, t), ncap) == sl.f(BF_M, t) ? 1 : 2;
+  }
+  __syncthreads();
   double smax = 0.0, tot = 0.0;
-  for (int t = tid; t < Pc; t += nth) {
-    const int n = sl.f(BF_G, t);
-    if (n == 0) continue;
-    const double* lst = sl.sval + sl.f(BF_COFF, t);
-    smax = fmax(smax, lst[0]);
-    double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc += lst[k] * lst[k];
-    const int mult = pair_mirror(sl.f(BF_M, t), ncap) == sl.f(BF_M, t) ? 1 : 2;
-    tot += mult * acc;
+  for (int e = tid; e < coffs[Pc]; e += nth) {
+    const double v = sl.sval[e];
+    smax = fmax(smax, v);
+    tot += cmult[find_block(coffs, Pc + 1, e)] * (v * v);
   }
   red[tid] = smax;
   __syncthreads();
@@ -2307,16 +2342,29 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
   }
   const int cap = st.chi_cap[g.inst];
   if (keep == -1) {
-    // 3. ranks of every alive candidate; order[rank] for rank <= cap
+    // 3. ranks of every alive candidate; order[rank] for rank <= cap.  The alive values
+    // of every list (a mirror list repeats its block's values) are staged in shared
+    // memory when they fit, so the binary searches below do not go to L2.
+    __shared__ double svs[SELECT_STAGE];
+    const bool staged = nalive <= SELECT_STAGE;
+    if (staged)
+      for (int e = tid; e < nalive; e += nth) {
+        const int l = find_block(lstart, NL + 1, e);
+        svs[e] = sl.sval[sl.f(BF_COFF, l >> 1) + (e - lstart[l])];
+      }
+    __syncthreads();
+    auto list_of = [&](int l) {
+      return staged ? svs + lstart[l] : sl.sval + sl.f(BF_COFF, l >> 1);
+    };
     for (int e = tid; e < nalive; e += nth) {
       const int l = find_block(lstart, NL + 1, e);
       const int k = e - lstart[l];
-      const double sv = sl.sval[sl.f(BF_COFF, l >> 1) + k];
+      const double sv = list_of(l)[k];
       const int mpair = lpair[l];
       int rank = 0;
       for (int l2 = 0; l2 < NL; ++l2) {
         if (lalive[l2] == 0) continue;
-        rank += count_before(sl.sval + sl.f(BF_COFF, l2 >> 1), lalive[l2], lpair[l2], sv, mpair, k);
+        rank += count_before(list_of(l2), lalive[l2], lpair[l2], sv, mpair, k);
       }
       if (rank <= cap) sl.order[rank] = e;
     }
@@ -2324,7 +2372,7 @@ __global__ void __launch_bounds__(1024) k_select(MpoDev st, SlotWS ws, const Gat
     if (tid == 0) {
       auto sval_of = [&](int e) {
         const int l = find_block(lstart, NL + 1, e);
-        return sl.sval[sl.f(BF_COFF, l >> 1) + (e - lstart[l])];
+        return list_of(l)[e - lstart[l]];
       };
       int jc = cap;
       while (jc > 0 && sval_of(sl.order[jc]) >= sval_of(sl.order[jc - 1]) * (1.0 - TIE_REL)) --jc;
@@ -2422,17 +2470,26 @@ __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const Gat
   const int tid = threadIdx.x, nth = blockDim.x;
   __shared__ int kpre[MPO_PC_MAX + 1];
   __shared__ int segA[MPO_P_MAX + 1], segB[MPO_P_MAX + 1];
+  extern __shared__ double rinv[];  // 1 / lambda of bonds A (first D) and B (next D)
   const long long bA = (long long)g.inst * (M + 1) + g.j, bB = bA + 2;
   for (int t = tid; t <= Pc; t += nth) kpre[t] = sl.f(BF_KOFF, t);
   for (int p = tid; p <= P; p += nth) {
     segA[p] = st.segoff[bA * (P + 1) + p];
     segB[p] = st.segoff[bB * (P + 1) + p];
   }
-  __syncthreads();
   const int* chA = st.charge + bA * D;
   const int* chB = st.charge + bB * D;
   const double* lA = st.lam + bA * D;
   const double* lB = st.lam + bB * D;
+  // the reciprocals once per CTA (an FP64 division is a long instruction sequence here)
+  {
+    const int nA = st.chi[bA], nB = st.chi[bB];
+    for (int i = tid; i < nA; i += nth) rinv[i] = 1.0 / lA[i];
+    for (int i = tid; i < nB; i += nth) rinv[D + i] = 1.0 / lB[i];
+  }
+  __syncthreads();
+  const double* rA = rinv;
+  const double* rB = rinv + D;
   double2* G1 = st.gam + ((long long)g.inst * M + g.j) * D * D;
   double2* G2 = G1 + (long long)D * D;
   const int items = sl.scal[SS_NITEMS];
@@ -2456,19 +2513,19 @@ __global__ void __launch_bounds__(256) k_resplit(MpoDev st, SlotWS ws, const Gat
     for (int i = tid; i < r; i += nth) {
       const double2 x = side == 1 ? cscale(to_d2(wk[i]), isig) : to_d2(vk[i]);
       const int a = rmap[i];
-      G1[(long long)a * D + beta] = cscale(x, 1.0 / lA[a]);
+      G1[(long long)a * D + beta] = cscale(x, rA[a]);
       if (mir) {
         const int am = mirror_index(segA, chA, a, ncap, st.err);
-        if (am >= 0) G1[(long long)am * D + betam] = cscale(cconj(x), 1.0 / lA[am]);
+        if (am >= 0) G1[(long long)am * D + betam] = cscale(cconj(x), rA[am]);
       }
     }
     for (int qq = tid; qq < c; qq += nth) {
       const double2 y = side == 1 ? cconj(to_d2(vk[qq])) : cscale(cconj(to_d2(wk[qq])), isig);
       const int b = cmap[qq];
-      G2[(long long)beta * D + b] = cscale(y, 1.0 / lB[b]);
+      G2[(long long)beta * D + b] = cscale(y, rB[b]);
       if (mir) {
         const int bm = mirror_index(segB, chB, b, ncap, st.err);
-        if (bm >= 0) G2[(long long)betam * D + bm] = cscale(cconj(y), 1.0 / lB[bm]);
+        if (bm >= 0) G2[(long long)betam * D + bm] = cscale(cconj(y), rB[bm]);
       }
     }
   }
@@ -2610,7 +2667,7 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) record_stage_event(ev[5], st);
   k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
   if (ev) record_stage_event(ev[6], st);
-  k_resplit<R><<<dim3(per, ngates), 256, 0, st>>>(s, ws, d_gates);
+  k_resplit<R><<<dim3(per, ngates), 256, 2 * (size_t)s.D * sizeof(double), st>>>(s, ws, d_gates);
   if (ev) record_stage_event(ev[7], st);
 }
 
@@ -2620,6 +2677,11 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
 cudaError_t gate_module_init() {
   sm_count();
   cudaError_t e = cudaFuncSetAttribute(k_svd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
+  // k_resplit: 1 / lambda of two bonds, D <= 4096 (the capacity limit of mpo_init_*)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_resplit<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_resplit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4096 * 8);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_theta<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)theta_smem_bytes(MPO_NCAP_MAX, sizeof(double2)));
