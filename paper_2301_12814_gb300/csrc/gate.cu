@@ -1188,8 +1188,9 @@ __device__ void seed_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 // A block whose Jacobi work would hold one SM long after the rest of the layer has
 // finished runs on a whole thread-block cluster (K CTAs, one per SM): a parallel
 // one-sided block Jacobi.  The n columns of W (length h) and of V (length n) are cut
-// into 2K column blocks of width b = ceil(n / 2K); a round-robin tournament over the
-// blocks gives every CTA one block pair per round (2K - 1 rounds per sweep).  A CTA
+// into 2K w column blocks of width b = ceil(n / 2K w), w the smallest power of two
+// (<= 8) for which a CTA's two blocks fit in shared memory; a round-robin tournament
+// over the blocks gives every CTA w block pairs per round (2K w - 1 rounds per sweep).  A CTA
 // stages its two blocks in shared memory, orthogonalises every column of one block
 // against every column of the other (b rounds of b disjoint pairs, one warp per
 // pair; in the first round of a sweep also the pairs inside each block), writes them
@@ -1323,8 +1324,12 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
   typedef typename Prec<R>::C C;
   const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  const int nb = 2 * K, b = (n + nb - 1) / nb;
   const size_t room = L.total - L.data;
+  // 2 K wb column blocks: wb (1..8) grows until a CTA's two blocks of W and V fit in
+  // shared memory; each CTA then takes wb block pairs of a round one after another
+  int wb = 1;
+  while (wb < 8 && (size_t)2 * ((n + 2 * K * wb - 1) / (2 * K * wb)) * ((size_t)h + n) * sizeof(C) > room) wb *= 2;
+  const int nb = 2 * K * wb, b = (n + nb - 1) / nb;
   const bool w_st = (size_t)2 * b * h * sizeof(C) <= room;
   const bool v_st = w_st && (size_t)2 * b * ((size_t)h + n) * sizeof(C) <= room;
   C* sW = reinterpret_cast<C*>(smem + L.data);
@@ -1336,8 +1341,9 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
     wr2 = 0.f;
     __syncthreads();
     for (int rho = 0; rho < nb - 1; ++rho) {
+     for (int pi = kr; pi < nb / 2; pi += K) {
       int I, J;
-      circle_pair(rho, kr, nb, I, J);
+      circle_pair(rho, pi, nb, I, J);
       const int i0 = I * b, j0 = J * b;
       const int nI = max(0, min(n, i0 + b) - i0), nJ = max(0, min(n, j0 + b) - j0);
       const int nl = nI + nJ;
@@ -1392,6 +1398,8 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
         if (v_st)
           for (long long e = tid; e < (long long)nl * n; e += nth) gV[(long long)gcol((int)(e / n)) * n + e % n] = sV[e];
       }
+      __syncthreads();  // the staging buffers are refilled for the next block pair
+     }
       cluster_exchange(cl);
     }
     // cluster-wide count of this sweep's rotations and its largest relative off-diagonal
