@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libgbsmpo.so")
 SOURCES = ["api.cu", "init.cu", "gate.cu", "obs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr", "-diag-suppress", "177"]
+         "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
 
 
 def _nvcc() -> str:

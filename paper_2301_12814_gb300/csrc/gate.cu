@@ -48,7 +48,6 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int TILE = 16;
-constexpr int MCH = 8;        // new-centre charges mixed per pass of the contraction
 constexpr double TIE_REL = 1e-9;
 constexpr int JACOBI_MAX_SWEEPS = 60;
 // Which blocks are factorised on a whole thread-block cluster (see the large-block
@@ -67,9 +66,10 @@ __device__ __forceinline__ unsigned long long svd_work(int n, int h) {
 }
 
 template <typename R> struct Prec;
-// tol_*: two-sided Jacobi on the Gram matrix; os_*: one-sided refinement on
-// W = Theta V; floor: singular values with s^2 <= floor * s_max^2 are dropped (the
-// refined values are accurate to a few ulps of s_max, not of s_max^2).
+// tol_* (FP32 only: the Gram seed is FP32 on both paths): two-sided Jacobi on the
+// Gram matrix; os_*: one-sided refinement on W = Theta V; floor: singular values with
+// s^2 <= floor * s_max^2 are dropped (the refined values are accurate to a few ulps of
+// s_max, not of s_max^2).
 // stop2: once the largest relative off-diagonal |w_p^dag w_q|^2 / (|w_p|^2 |w_q|^2) of a
 // one-sided sweep is below stop2, the iteration stops after this sweep: it leaves
 // off-diagonals of order stop2 (quadratic convergence), which perturb the singular
@@ -81,7 +81,6 @@ template <typename R> struct Prec;
 template <> struct Prec<double> {
   typedef double2 C;
   static constexpr double stop2 = 1e-12;
-  static constexpr double tol_rel = 1e-15, tol_abs = 1e-18;
   static constexpr double os_rel = 4e-15, os_abs = 1e-30;
   static constexpr double floor = 1e-28;
 };
@@ -95,23 +94,16 @@ template <> struct Prec<float> {
 };
 
 // ---- element helpers for real (self-mirror) and complex Jacobi ----
-__device__ __forceinline__ double re(double x) { return x; }
 __device__ __forceinline__ float re(float x) { return x; }
-__device__ __forceinline__ double re(double2 x) { return x.x; }
 __device__ __forceinline__ float re(float2 x) { return x.x; }
-__device__ __forceinline__ double absv(double x) { return fabs(x); }
 __device__ __forceinline__ float absv(float x) { return fabsf(x); }
-__device__ __forceinline__ double absv(double2 x) { return hypot(x.x, x.y); }
 __device__ __forceinline__ float absv(float2 x) { return hypotf(x.x, x.y); }
-__device__ __forceinline__ double cj(double x) { return x; }
 __device__ __forceinline__ float cj(float x) { return x; }
 __device__ __forceinline__ double2 cj(double2 x) { return make_double2(x.x, -x.y); }
 __device__ __forceinline__ float2 cj(float2 x) { return make_float2(x.x, -x.y); }
-__device__ __forceinline__ double mulv(double a, double b) { return a * b; }
 __device__ __forceinline__ float mulv(float a, float b) { return a * b; }
 __device__ __forceinline__ double2 mulv(double2 a, double2 b) { return cmul(a, b); }
 __device__ __forceinline__ float2 mulv(float2 a, float2 b) { return cmul(a, b); }
-__device__ __forceinline__ double lin(double c, double x, double s, double y) { return c * x + s * y; }
 __device__ __forceinline__ float lin(float c, float x, float s, float y) { return c * x + s * y; }
 __device__ __forceinline__ double2 lin(double c, double2 x, double s, double2 y) {
   return make_double2(c * x.x + s * y.x, c * x.y + s * y.y);
@@ -120,21 +112,15 @@ __device__ __forceinline__ float2 lin(float c, float2 x, float s, float2 y) {
   return make_float2(c * x.x + s * y.x, c * x.y + s * y.y);
 }
 template <typename E, typename R> __device__ __forceinline__ E divr(E g, R h);
-template <> __device__ __forceinline__ double divr<double, double>(double g, double h) { return g / h; }
 template <> __device__ __forceinline__ float divr<float, float>(float g, float h) { return g / h; }
-template <> __device__ __forceinline__ double2 divr<double2, double>(double2 g, double h) {
-  return make_double2(g.x / h, g.y / h);
-}
 template <> __device__ __forceinline__ float2 divr<float2, float>(float2 g, float h) {
   return make_float2(g.x / h, g.y / h);
 }
 template <typename E> __device__ __forceinline__ E unit_e();
-template <> __device__ __forceinline__ double unit_e<double>() { return 1.0; }
 template <> __device__ __forceinline__ float unit_e<float>() { return 1.0f; }
 template <> __device__ __forceinline__ double2 unit_e<double2>() { return make_double2(1.0, 0.0); }
 template <> __device__ __forceinline__ float2 unit_e<float2>() { return make_float2(1.0f, 0.0f); }
 template <typename E> __device__ __forceinline__ E zero_e();
-template <> __device__ __forceinline__ double zero_e<double>() { return 0.0; }
 template <> __device__ __forceinline__ float zero_e<float>() { return 0.0f; }
 template <> __device__ __forceinline__ double2 zero_e<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 zero_e<float2>() { return make_float2(0.0f, 0.0f); }
@@ -495,7 +481,7 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
   Slot sl = get_slot(ws, s);
   if (sl.scal[SS_STATUS]) return;
   const GateDesc g = gates[s];
-  const int ncap = st.ncap, q = ncap + 1, P = st.P, M = st.M, D = st.D;
+  const int ncap = st.ncap, P = st.P, M = st.M, D = st.D;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nfk = fock_off(ncap + 1);
   const ThetaSmem TL = theta_smem(ncap, sizeof(C));
