@@ -1,0 +1,122 @@
+"""Two run protocols of the paper's experiments (App. A), driven over the C ABI.
+
+Every gate still runs in the library's kernels; this module only decides how far to
+run and with which bond dimension.
+
+* ``ee_over_depth``: apply the mesh layer by layer and record, after each layer, the
+  largest operator entanglement over the cuts between modes; stop once the running
+  maximum has not increased for ``patience`` layers (App. A: simulate until there is no
+  MPO EE increase for at least 10 layers; only the maximum over depth matters).
+* ``bond_dimension_search``: run the full mesh with a small bond dimension and double
+  it while the truncation error 1 - Tr rho exceeds the target (App. A: start small,
+  double while the error exceeds 0.02), then narrow the bracket by bisection a few
+  more times (App. A: the bond dimension is refined a few more times).
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import mpo as _mpo
+
+
+def plateau_stop(values: Sequence[float], patience: int) -> Optional[int]:
+    """Index of the layer after which a run stops: the first layer whose running
+    maximum has not strictly increased for ``patience`` consecutive layers (None if
+    that never happens)."""
+    best = -np.inf
+    since = 0
+    for i, v in enumerate(values):
+        if v > best:
+            best = v
+            since = 0
+        else:
+            since += 1
+            if since >= patience:
+                return i
+    return None
+
+
+def _layers(layer_of: Sequence[int]) -> List[np.ndarray]:
+    layer_of = np.asarray(layer_of)
+    return [np.nonzero(layer_of == l)[0] for l in range(int(layer_of.max()) + 1)] if layer_of.size else []
+
+
+def ee_over_depth(M: int, d: int, r, eta, chi: Optional[int], k: Sequence[int], theta: Sequence[float],
+                  phi: Sequence[float], layer_of: Sequence[int], patience: int = 10,
+                  precision: str = "fp64") -> Dict[str, object]:
+    """Apply the gates layer by layer (``layer_of[g]`` = layer of gate g; gates of one
+    layer act on disjoint mode pairs) and stop by the App. A rule.
+
+    Returns ``{"max_ee": [largest S over the cuts 1..M-1 after each simulated layer],
+    "layers": simulated layers, "stopped": whether the rule fired, "max_over_depth":
+    the largest of them, "trace": Tr rho at the end}``."""
+    k = np.asarray(k, dtype=np.int32)
+    theta = np.asarray(theta, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision)
+    try:
+        max_ee: List[float] = []
+        stopped = False
+        for idx in _layers(layer_of):
+            if idx.size:
+                G.sweep_mesh([idx.size], k[idx], theta[idx], phi[idx])
+            S = G.operator_entropy()[0][0]
+            max_ee.append(float(np.max(S[1:M])))
+            if plateau_stop(max_ee, patience) is not None:
+                stopped = True
+                break
+        tr = G.observables(normalize=False)[0][0]
+    finally:
+        G.close()
+    return {"max_ee": max_ee, "layers": len(max_ee), "stopped": stopped,
+            "max_over_depth": max(max_ee) if max_ee else 0.0, "trace": float(tr)}
+
+
+def _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision) -> float:
+    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision)
+    try:
+        G.sweep_mesh([len(k)], k, theta, phi, final_phase)
+        return float(1.0 - G.observables(normalize=False)[0][0])
+    finally:
+        G.close()
+
+
+def bond_dimension_search(M: int, d: int, r, eta, k: Sequence[int], theta: Sequence[float],
+                          phi: Sequence[float], final_phase=None, chi0: int = 8, target: float = 0.02,
+                          refine: int = 3, chi_limit: int = 4096, precision: str = "fp64") -> Dict[str, object]:
+    """The smallest bond dimension found whose full-mesh truncation error 1 - Tr rho is
+    at most ``target``: double from ``chi0`` until the error is within the target, then
+    bisect the last bracket ``refine`` times.  Returns ``{"chi": ..., "error": ...,
+    "visited": [(chi, error), ...]}`` (``chi`` is None if ``chi_limit`` is reached)."""
+    k = np.asarray(k, dtype=np.int32)
+    theta = np.asarray(theta, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    visited = []
+
+    def err(chi):
+        e = _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision)
+        visited.append((chi, e))
+        return e
+
+    chi = chi0
+    e = err(chi)
+    while e > target:
+        if chi >= chi_limit:
+            return {"chi": None, "error": e, "visited": visited}
+        chi = min(2 * chi, chi_limit)
+        e = err(chi)
+    lo, hi, e_hi = chi // 2, chi, e  # error(lo) > target (or lo below chi0), error(hi) <= target
+    if chi == chi0:
+        lo = 0
+    for _ in range(refine):
+        if hi - lo <= 1:
+            break
+        mid = (lo + hi) // 2
+        e_mid = err(mid)
+        if e_mid <= target:
+            hi, e_hi = mid, e_mid
+        else:
+            lo = mid
+    return {"chi": hi, "error": e_hi, "visited": visited}
