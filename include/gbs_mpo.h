@@ -169,6 +169,17 @@ void mpo_plan_destroy(mpo_plan p);
 mpo_status mpo_observables(mpo_handle h, double* trace, double* n_mean, double* n2_mean,
                            int normalize_by_trace);
 
+/* Probability removed by the truncation of the initial state (App. A: d is the
+ * smallest local dimension for which less than 1% of the probability is cut).
+ *   tail [batch]  1 - Tr(P_cap (x)_j rho_j P_cap), where rho_j is mode j's lossy
+ *                 squeezed vacuum from amplitudes normalised in the infinite Fock
+ *                 space and truncated at d levels before loss (App. C, App. B), and
+ *                 P_cap keeps total photon numbers <= n_cap (App. A: the left-most
+ *                 charge is the total photon number).
+ * Fixed when the handle is made (the mesh is unitary on the kept space); host
+ * memory; MPO_ERR_ARG for a NULL argument.  Does not synchronise. */
+mpo_status mpo_truncated_probability(mpo_handle h, double* tail);
+
 /* Operator entanglement of the U(1) MPO at every bond (Method, Eq. `schmidt`;
  * App. B: p = lambda^2 / sum lambda^2, S = -sum p log2 p):
  *   S             [batch*(M+1)]  bonds 0..M

@@ -131,9 +131,11 @@ class U1MPO:
         construction written out."""
         M, cap = self.M, self.n_cap
         self.rho_modes = []
+        kept_modes = 1.0
         for j in range(M):
-            rho_j, _ = fock.lossy_mode_state(r[j], eta[j], self.d)
+            rho_j, tail_j = fock.lossy_mode_state(r[j], eta[j], self.d)
             self.rho_modes.append(rho_j[:cap + 1, :cap + 1])
+            kept_modes *= 1.0 - tail_j
         w = [np.abs(rj) ** 2 for rj in self.rho_modes]
         R2 = [None] * (M + 1)
         R2[M] = np.zeros((cap + 1, cap + 1)); R2[M][0, 0] = 1.0
@@ -161,6 +163,9 @@ class U1MPO:
             t = nt
         T = float(t.sum())
         self.cap_trace = T
+        # App. A: the probability cut by the local dimension (each mode's squeezed
+        # vacuum keeps its first d Fock levels) and then by the photon-number cap
+        self.truncated_probability = 1.0 - kept_modes * T
         self.charges: List[np.ndarray] = []
         self.lam: List[np.ndarray] = []
         for b in range(M + 1):

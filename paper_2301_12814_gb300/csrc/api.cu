@@ -34,6 +34,7 @@ struct mpo_ctx {
   int* d_err = nullptr;
   int* d_chicap = nullptr;
   std::vector<int> chicap;
+  std::vector<double> kept;   // [B] probability kept by the Fock and photon-number cut
   // gate workspace
   void* ws_buf = nullptr;
   SlotWS ws{};
@@ -331,6 +332,12 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
   cudaMemcpyAsync(d_re + (size_t)B * M, eta, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   launch_init(h->dev, d_re, d_re + (size_t)B * M, d, d_scr, h->stream);
   cudaError_t e = cudaGetLastError();
+  // k_init leaves each instance's kept probability T in the first slot after its
+  // per-mode tables; one strided copy gathers them before the scratch is freed.
+  h->kept.assign(B, 0.0);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(h->kept.data(), sizeof(double), d_scr + (per - 64), per * sizeof(double),
+                          sizeof(double), B, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(d_scr); cudaFree(d_re);
   if (e != cudaSuccess) return fail(cuda_status(e));
@@ -621,6 +628,12 @@ mpo_status mpo_observables(mpo_handle h, double* trace, double* n_mean, double* 
       if (n2_mean) n2_mean[(size_t)i * M + j] = o[1 + M + j] * sc;
     }
   }
+  return MPO_OK;
+}
+
+mpo_status mpo_truncated_probability(mpo_handle h, double* tail) {
+  if (!h || !tail) return MPO_ERR_ARG;
+  for (int i = 0; i < h->B; ++i) tail[i] = 1.0 - h->kept[i];
   return MPO_OK;
 }
 

@@ -11,6 +11,11 @@ run and with which bond dimension.
   it while the truncation error 1 - Tr rho exceeds the target (App. A: start small,
   double while the error exceeds 0.02), then narrow the bracket by bisection a few
   more times (App. A: the bond dimension is refined a few more times).
+* ``choose_d``: the smallest local dimension d whose initial state loses less than a
+  threshold of the probability to the Fock and photon-number cut (App. A: d is chosen
+  so that under 1% is truncated; the left-most charge is the total photon number, so
+  the cap n_cap = d - 1 binds the whole register and d grows with r and with the
+  number of squeezed inputs).
 """
 from __future__ import annotations
 
@@ -120,3 +125,22 @@ def bond_dimension_search(M: int, d: int, r, eta, k: Sequence[int], theta: Seque
         else:
             lo = mid
     return {"chi": hi, "error": e_hi, "visited": visited}
+
+
+def choose_d(M: int, r, eta, threshold: float = 0.01, d_min: int = 2, d_max: int = 16) -> Dict[str, object]:
+    """Scan d = d_min .. d_max and return the first whose truncated probability
+    (``MPO.truncated_probability``, the kernel-computed 1 - Tr(P_cap (x) rho_j P_cap)
+    with n_cap = d - 1) is below ``threshold``.  The kept set only grows with d, so the
+    first hit is the smallest.  Returns ``{"d": ..., "tail": ..., "visited":
+    [(d, tail), ...]}`` (``d`` is None if d_max is not enough)."""
+    visited = []
+    for d in range(int(d_min), int(d_max) + 1):
+        G = _mpo.MPO(M, d, r, eta, chi_max=1)
+        try:
+            tail = float(G.truncated_probability()[0])
+        finally:
+            G.close()
+        visited.append((d, tail))
+        if tail < threshold:
+            return {"d": d, "tail": tail, "visited": visited}
+    return {"d": None, "tail": visited[-1][1] if visited else None, "visited": visited}

@@ -24,7 +24,7 @@ EXPORTS = [
     "mpo_init_lossy_squeezed", "mpo_reset", "mpo_apply_bs", "mpo_sweep_mesh", "mpo_plan_mesh",
     "mpo_plan_run", "mpo_plan_discarded", "mpo_plan_launches", "mpo_plan_profile", "mpo_plan_stage_times",
     "mpo_plan_destroy",
-    "mpo_observables", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
+    "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
 ]
 
@@ -73,6 +73,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_svd_cluster_shape": (_i, [_ip, _ip, _ip, _ip]),
         "mpo_plan_destroy": (None, [_p]),
         "mpo_observables": (_i, [_p, _dp, _dp, _dp, _i]),
+        "mpo_truncated_probability": (_i, [_p, _dp]),
         "mpo_operator_entropy": (_i, [_p, _dp, _dp, _dp]),
         "mpo_get_bonds": (_i, [_p, _i, _i, _ip, _dp, _ip]),
         "mpo_bond_capacity": (_i, [_p]),
@@ -236,6 +237,13 @@ class MPO:
         _check(_lib().mpo_observables(self._h, _d(tr), _d(n1), _d(n2), 1 if normalize else 0),
                "mpo_observables")
         return tr, n1.reshape(B, M), n2.reshape(B, M)
+
+    def truncated_probability(self) -> np.ndarray:
+        """[batch] probability cut from the initial state by the local dimension d and
+        the photon-number cap (mpo_truncated_probability)."""
+        tail = np.zeros(self.batch)
+        _check(_lib().mpo_truncated_probability(self._h, _d(tail)), "mpo_truncated_probability")
+        return tail
 
     def operator_entropy(self):
         B, M = self.batch, self.M

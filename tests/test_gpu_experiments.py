@@ -60,3 +60,39 @@ def test_bond_dimension_search_vs_oracle(ex):
         assert abs(e - (1.0 - tr)) <= 1e-10 * max(tr, 1e-300) + 1e-12, (chi, e, 1.0 - tr)
     # doubling then bisection: the answer passes, every smaller visited value failed
     assert all(e > 0.4 for c, e in res["visited"] if c < res["chi"])
+
+
+def test_truncated_probability_vs_oracle(ex):
+    """Per-instance truncated probability of a batched handle (kernel-computed kept
+    probability) against the oracle's, with different r and eta per instance and an
+    explicit photon-number cap below d - 1."""
+    from paper_2301_12814_gb300 import mpo
+    rng = np.random.default_rng(7)
+    M, d, B = 6, 8, 3
+    r = rng.uniform(0.4, 1.2, (B, M))
+    eta = rng.uniform(0.2, 0.9, (B, M))
+    for n_cap in (None, 5):
+        G = mpo.MPO(M, d, r, eta, chi_max=16, batch=B, n_cap=n_cap)
+        try:
+            got = G.truncated_probability()
+        finally:
+            G.close()
+        for i in range(B):
+            want = u1mpo.U1MPO(M, d, r[i], eta[i], n_cap=n_cap).truncated_probability
+            assert abs(got[i] - want) <= 1e-13, (n_cap, i, got[i], want)
+
+
+def test_choose_d_vs_oracle(ex):
+    """App. A's choice of d: every visited d carries the oracle's tail, the answer is
+    the first below 1%, and each smaller d was at or above it."""
+    M = 8
+    r = [0.9] * 2 + [0.0] * (M - 2)  # N = M / 4 squeezed inputs, as in App. A
+    eta = [0.5] * M
+    res = ex.choose_d(M, r, eta, threshold=0.01, d_min=4)
+    want_d = next(d for d in range(4, 17) if u1mpo.U1MPO(M, d, r, eta).truncated_probability < 0.01)
+    assert res["d"] == want_d and res["tail"] < 0.01
+    for d, tail in res["visited"]:
+        want = u1mpo.U1MPO(M, d, r, eta).truncated_probability
+        assert abs(tail - want) <= 1e-13, (d, tail, want)
+    assert all(t >= 0.01 for d, t in res["visited"] if d < res["d"])
+    assert res["visited"][-1][0] == res["d"]

@@ -225,3 +225,42 @@ def test_pins_catch_planted_mistakes(monkeypatch, mistake):
     P.run_mesh(mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
     monkeypatch.undo()
     assert np.abs(P.to_dense() - D.rho).max() > 1e-3
+
+
+def _photon_count_kept(r, eta, d, n_cap):
+    """Kept probability from photon-number statistics alone: a squeezed vacuum holds
+    2m photons with the negative-binomial weight NB(m; 1/2, 1/cosh^2 r) (its
+    generating function is (1 - tanh^2 r)^(1/2) (1 - x tanh^2 r)^(-1/2)); keep n < d,
+    thin each photon with survival eta (binomial), keep a total <= n_cap."""
+    from scipy import stats
+    tot = np.zeros(1); tot[0] = 1.0
+    for rj, ej in zip(r, eta):
+        q = np.zeros(d)
+        for n in range(0, d, 2):
+            pn = stats.nbinom.pmf(n // 2, 0.5, 1.0 / math.cosh(rj) ** 2)
+            q[:n + 1] += pn * stats.binom.pmf(np.arange(n + 1), n, ej)
+        tot = np.convolve(tot, q)
+    return float(tot[:n_cap + 1].sum())
+
+
+@pytest.mark.parametrize("M,d,n_cap", [(4, 6, None), (5, 5, 3), (3, 9, None), (6, 4, 2)])
+def test_truncated_probability_matches_photon_statistics(M, d, n_cap):
+    """App. A's truncated probability from the oracle's Kraus-built state equals the
+    same number from squeezed-vacuum photon statistics and binomial loss."""
+    rng = np.random.default_rng(M * 100 + d)
+    r = rng.uniform(0.3, 1.2, M)
+    eta = rng.uniform(0.2, 0.9, M)
+    P = u1mpo.U1MPO(M, d, r, eta, n_cap=n_cap)
+    cap = d - 1 if n_cap is None else n_cap
+    assert abs(P.truncated_probability - (1.0 - _photon_count_kept(r, eta, d, cap))) < 1e-13
+
+
+def test_truncated_probability_limits():
+    """No squeezing truncates nothing; the tail shrinks as d grows and vanishes in the
+    limit (the squeezed vacuum's weights sum to one)."""
+    M = 3
+    P = u1mpo.U1MPO(M, 5, [0.0] * M, [0.5] * M)
+    assert abs(P.truncated_probability) < 1e-15
+    tails = [u1mpo.U1MPO(M, d, [0.8] * M, [0.6] * M).truncated_probability for d in range(3, 17)]
+    assert all(a > b for a, b in zip(tails, tails[1:]))
+    assert tails[-1] < 2e-3 and tails[0] > 0.1
