@@ -363,6 +363,164 @@ def run_native(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+ASYM_WORKLOAD = "asymptotic_fig1"
+ASYM_METRIC = "App. C asymptotic operator-EE estimates/s over the Fig. 1 grid (r=0.88, n_max=8)"
+
+
+def oracle_asymptotic(n_points: int, repeats: int = 1) -> dict:
+    env = dict(os.environ)
+    env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-m", "oracle.timing", "asymptotic", str(n_points), str(repeats)],
+                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def asym_flops(n_max: int, sweeps: np.ndarray) -> float:
+    """Algorithmic FP64 flops of the block Jacobi: per visited column pair of a block of
+    nb columns, 6 nb for the three dot products; 6 nb more for the rotation in every
+    sweep but the last (which by definition rotates nothing)."""
+    L = n_max + 1
+    E = n_max // 2 + 1
+    O = L - E
+    nbs = [E * (E + 1) // 2 + O * (O + 1) // 2, E * O, E * (E - 1) // 2 + O * (O - 1) // 2, E * O]
+    sw = sweeps.reshape(-1, 4)
+    tot = 0.0
+    for j, nb in enumerate(nbs):
+        pairs = nb * (nb - 1) / 2
+        tot += float(np.sum(sw[:, j] * pairs * 6 * nb + np.maximum(sw[:, j] - 1, 0) * pairs * 6 * nb))
+    return tot
+
+
+def run_asymptotic(args, ws, rank, local):
+    """The App. C estimator over the Fig. 1 grid: one step = every grid point's
+    mode spectrum and entropies (two kernel launches on device-resident inputs)."""
+    import gbs_workloads as w
+    g = w.asymptotic_grid()
+    npts = g.size
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        res = oracle_asymptotic(npts, repeats=args.warmup + args.steps)
+        t = res["seconds"][args.warmup:] or res["seconds"]
+        ms = 1e3 * float(np.mean(t))
+        val = npts / (ms / 1e3)
+        line = {"impl": "reference", "metric": ASYM_METRIC, "value": val, "unit": "estimates/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": g.name, "points": npts, "r": g.r, "n_max": g.n_max},
+                "cpu_baseline": {"value": val, "unit": "estimates/s", "cores": res["cores"], "kind": "oracle",
+                                 "sample": f"the whole grid ({npts} points) per step"},
+                "e2e": {"value": val, "unit": "estimates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+    import paper_2301_12814_gb300 as lib
+    from paper_2301_12814_gb300 import build as libbuild, experiments as ex
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mu = ex.transmission(g.N, g.beta, g.gamma)
+    K = (g.n_max + 1) ** 2
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        t_r = torch.full((npts,), g.r, dtype=torch.float64, device=dev)
+        t_mu = torch.tensor(mu, dtype=torch.float64, device=dev)
+        t_th = torch.full((npts,), math.pi / 4, dtype=torch.float64, device=dev)
+        S1 = torch.empty(npts, dtype=torch.float64, device=dev)
+        spec = torch.empty(npts * K, dtype=torch.float64, device=dev)
+        sw = torch.zeros(4 * npts, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    call = lambda: lib.mpo.asymptotic_ee_device(t_r, t_mu, t_th, g.n_max, S1, spec, sweeps=sw, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        call()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.6)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    clocks.mark()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        call()
+        ev[i][1].record(stream)
+    barrier()
+    clocks.mark()
+    time.sleep(0.3)
+    clocks.stop()
+    tot_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    value = aggregate_value(npts * args.steps, tot_ms, ws, dev)
+    if ws > 1:
+        tot_ms = ws * npts * args.steps / value * 1e3
+    S_dev = S1.cpu().numpy() * g.N
+    sweeps = sw.cpu().numpy()
+    # end to end through the public API: host arrays in, host entropies out
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        S_host = ex.asymptotic_ee(g.N, g.beta, g.gamma, g.r, g.n_max)["S1"]
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = aggregate_value(npts, 1e3 * float(np.mean(e2e_t)), ws, dev)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    ms_step = tot_ms / args.steps
+    fl = asym_flops(g.n_max, sweeps)
+    achieved = fl / (ms_step / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_asym_block (+ k_asym_finalize)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 SIMT FMA peak derived from 152 SMs x 2.07 GHz x 4 flop/clk/SM; "
+                               "MEASURED_PEAKS.json has only HBM and bf16 tensor peaks",
+                "traffic": None, "flops_per_launch": fl, "avg_launch_ms": ms_step,
+                "timing": "CUDA events around the two launches of each timed step"}
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        try:
+            res = oracle_asymptotic(npts)
+            err = float(np.max(np.abs(np.asarray(res["S"]) - S_dev) / np.maximum(np.abs(S_dev), 1e-300)))
+            cpu = {"value": res["points_per_s"][0], "unit": "estimates/s", "cores": res["cores"],
+                   "kind": "oracle", "sample": f"the whole grid ({npts} points, {res['seconds'][0]:.1f} s)",
+                   "max_rel_diff_vs_gpu": err}
+        except Exception as e:
+            cpu = {"value": None, "unit": "estimates/s", "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {str(e)[-200:]}"}
+    line = {
+        "metric": ASYM_METRIC, "value": value, "unit": "estimates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": g.name, "points": npts, "r": g.r, "n_max": g.n_max,
+                   "gamma": [0.25, 0.5, 1.0], "beta": [0.25, 0.5, 0.75, 1.0],
+                   "N_range": [float(g.N.min()), float(g.N.max())],
+                   "l2": "flushed: 512 MiB write before each timed step (untimed)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "estimates/s", "h2d_bytes_per_step": 24 * npts,
+                "d2h_bytes_per_step": 8 * npts + 16 * npts},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks.summary(),
+        "jacobi": {"sweeps_mean": float(sweeps.mean()), "sweeps_max": int(sweeps.max())},
+        "host_equals_device": bool(np.array_equal(S_host, S_dev)),
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,7 +535,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = _dist()
-    if args.impl == "reference":
+    if args.workload == ASYM_WORKLOAD:
+        run_asymptotic(args, ws, rank, local)
+    elif args.impl == "reference":
         run_reference(args, ws, rank)
     else:
         run_native(args, ws, rank, local)

@@ -10,7 +10,9 @@ inputs both sides consume:
   final diagonal phase screen;
 * the workload recipes (M, d, chi, r, eta, seeds) of the five standard workloads
   and the per-instance draws of the batched one;
-* a greedy layering of the gate list into layers of gates on disjoint mode pairs.
+* a greedy layering of the gate list into layers of gates on disjoint mode pairs;
+* the parameter grid of the asymptotic-entanglement sweep (Results, Fig. 1): numbers
+  N of squeezed inputs, surviving-photon prefactors beta and exponents gamma.
 
 The paper builds its interferometers as Haar-random global unitaries realised by
 an M-layer nearest-neighbour array (Appendix A); the decomposition used here is
@@ -31,7 +33,8 @@ import numpy as np
 
 __all__ = [
     "haar_unitary", "clements", "mesh_unitary", "gate_block", "Mesh",
-    "Workload", "workload", "WORKLOADS", "layer_schedule", "batched_instances",
+    "Workload", "workload", "WORKLOADS", "layer_schedule", "batched_instances", "AsymptoticGrid",
+    "asymptotic_grid",
 ]
 
 
@@ -222,3 +225,29 @@ WORKLOADS = {
     "M48_d8_chi512": lambda: _uniform("M48_d8_chi512", 48, 8, 512, 0.9, _sqrt_n_eta(48, 0.9), 3,
                                       "mixed_bf16"),
 }
+
+
+@dataclasses.dataclass
+class AsymptoticGrid:
+    """Flattened (N, beta, gamma) points of the asymptotic sweep at squeezing r and
+    photon cutoff n_max."""
+    name: str
+    N: np.ndarray
+    beta: np.ndarray
+    gamma: np.ndarray
+    r: float
+    n_max: int
+
+    @property
+    def size(self) -> int:
+        return int(self.N.size)
+
+
+def asymptotic_grid(n_N: int = 64, N_min: float = 10.0, N_max: float = 1e5, n_max: int = 8) -> AsymptoticGrid:
+    """Fig. 1's sweep: N_out = beta N^gamma surviving photons for gamma = 1/4, 1/2, 1
+    and beta = 0.25, 0.5, 0.75, 1 (a linear trend in beta is what the figure shows),
+    N at n_N log-spaced values in [N_min, N_max] (rounded to integers), r = 0.88 (about
+    one photon per squeezed mode), n_max = 8."""
+    Ns = np.unique(np.round(np.logspace(math.log10(N_min), math.log10(N_max), n_N)))
+    g, b, n = np.meshgrid([0.25, 0.5, 1.0], [0.25, 0.5, 0.75, 1.0], Ns, indexing="ij")
+    return AsymptoticGrid(f"asymptotic_fig1_{Ns.size}N", n.ravel(), b.ravel(), g.ravel(), 0.88, n_max)

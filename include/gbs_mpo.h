@@ -204,6 +204,44 @@ mpo_status mpo_sync(mpo_handle h);
 void mpo_destroy(mpo_handle h);
 const char* mpo_status_string(mpo_status s);
 
+/* Asymptotic operator entanglement of one squeezed input mode (App. C): the estimate
+ * the paper uses for system sizes beyond direct MPO simulation (Results, Fig. 1).
+ * For each point i: the squeezed vacuum of r[i] truncated at n_max photons (App. C),
+ * pure loss of transmission mu[i] with the state and Kraus operators truncated at
+ * n_max (Eq. `lossy`), the split <k_u, k_d|U|n> = sqrt(C(n, k_u)) cos^k_u sin^k_d of
+ * theta[i] (Eq. `transform` / `kun`; pi/4 in the asymptotic limit), vectorisation
+ * X[(k_u, k_u'), (k_d, k_d')] = rho_out[k_u, k_d; k_u', k_d'], and the eigenvalues of
+ * tr_u |rho_out>><<rho_out| (the squared singular values of X) normalised to sum 1.
+ * The system estimate is N times S1 at mu = beta N^gamma / N; the caller forms it.
+ *   npts      number of points (0 is a no-op)
+ *   n_max     photon cutoff, 1 <= n_max <= MPO_ASYM_NMAX
+ *   r, mu, theta [npts]  squeezing (0..3), transmission (0..1), split angle (finite)
+ *   alpha     Renyi order (> 0) for S_alpha; ignored when S_alpha is NULL
+ *   S1        [npts]     von Neumann entropy of the normalised spectrum, bits
+ *   S_alpha   [npts]     log2(sum p^alpha) / (1 - alpha) (S1 at alpha = 1), nullable
+ *   spectrum  [npts*ld]  normalised eigenvalues, descending, (n_max+1)^2 per point;
+ *                        nullable; ld >= (n_max+1)^2
+ * Host pointers; allocates and frees its own device memory; synchronises.  Errors:
+ * MPO_ERR_ARG (sizes, ranges, NULL), MPO_ERR_NUMERIC (a Jacobi sweep cap reached),
+ * MPO_ERR_NOT_BUILT (no GPU), MPO_ERR_OOM / MPO_ERR_CUDA. */
+#define MPO_ASYM_NMAX 23
+mpo_status mpo_asymptotic_ee(int npts, int n_max, const double* r, const double* mu,
+                             const double* theta, double alpha, double* S1, double* S_alpha,
+                             double* spectrum, int ld);
+
+/* The same on DEVICE pointers with no allocation and no synchronisation: the two
+ * kernels are issued on cuda_stream (NULL = legacy default) and the outputs are ready
+ * when the stream reaches that point.  spectrum [npts*ld] is required (it is also the
+ * workspace); sweeps [4*npts] (nullable) receives the Jacobi sweeps of each point's
+ * four blocks (symmetric/even, symmetric/odd, antisymmetric/even, antisymmetric/odd
+ * under the swap (k_u, k_d) <-> (k_u', k_d') and by photon-number parity); a value
+ * above 40 means the sweep cap was reached.  Inputs are not range-checked on the
+ * device: values outside the ranges above give meaningless numbers, never a fault.
+ * MPO_ERR_ARG for sizes and NULLs, MPO_ERR_CUDA if a launch fails. */
+mpo_status mpo_asymptotic_ee_device(int npts, int n_max, const double* r, const double* mu,
+                                    const double* theta, double alpha, double* S1, double* S_alpha,
+                                    double* spectrum, int ld, int* sweeps, void* cuda_stream);
+
 /* Observables of one MPO held in buffers the caller owns, with no allocation.
  * The paper has no counterpart: this is a library-interface addition for callers
  * that cannot allocate device memory when they need the observables -- code inside

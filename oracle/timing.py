@@ -41,7 +41,30 @@ def run(name: str, n_gates: int, repeats: int = 1) -> dict:
     }
 
 
+def run_asymptotic(n_points: int, repeats: int = 1) -> dict:
+    """The App. C estimator of the oracle on the first n_points of the Fig. 1 grid."""
+    import gbs_workloads as w
+    from . import asymptotic
+    g = w.asymptotic_grid()
+    n = min(n_points, g.size)
+    times, S = [], []
+    for _ in range(max(1, repeats)):
+        t0 = time.perf_counter()
+        S = [asymptotic.system_entropy(int(g.N[i]), float(g.beta[i]), float(g.gamma[i]), g.r, g.n_max)
+             for i in range(n)]
+        times.append(time.perf_counter() - t0)
+    threads = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    return {"workload": g.name, "points": n, "seconds": times, "points_per_s": [n / t for t in times],
+            "S": S, "cores": 1 if all(v == "1" for v in threads.values()) else os.cpu_count(),
+            "threads_env": threads}
+
+
 if __name__ == "__main__":
+    if sys.argv[1] == "asymptotic":
+        n = int(sys.argv[2])
+        rep = int(sys.argv[3]) if len(sys.argv) > 3 else 1
+        print(json.dumps(run_asymptotic(n, rep)))
+        sys.exit(0)
     name = sys.argv[1]
     n = int(sys.argv[2])
     rep = int(sys.argv[3]) if len(sys.argv) > 3 else 1

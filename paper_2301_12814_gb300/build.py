@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbsmpo.so")
-SOURCES = ["api.cu", "init.cu", "gate.cu", "obs.cu"]
+SOURCES = ["api.cu", "init.cu", "gate.cu", "obs.cu", "asym.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]

@@ -16,9 +16,14 @@ run and with which bond dimension.
   so that under 1% is truncated; the left-most charge is the total photon number, so
   the cap n_cap = d - 1 binds the whole register and d grows with r and with the
   number of squeezed inputs).
+* ``asymptotic_ee`` / ``n_max_convergence``: the App. C estimate N S(mu = beta N^gamma / N)
+  behind Fig. 1 (EE against the number N of squeezed inputs for surviving photons
+  N_out = beta N^gamma, r = 0.88, n_max = 8) and its convergence in the photon cutoff
+  (Fig. 1(d): N = 50, beta = 1, gamma = 1/2).
 """
 from __future__ import annotations
 
+import math
 from typing import Dict, List, Optional, Sequence
 
 import numpy as np
@@ -144,3 +149,34 @@ def choose_d(M: int, r, eta, threshold: float = 0.01, d_min: int = 2, d_max: int
         if tail < threshold:
             return {"d": d, "tail": tail, "visited": visited}
     return {"d": None, "tail": visited[-1][1] if visited else None, "visited": visited}
+
+
+def transmission(N, beta, gamma) -> np.ndarray:
+    """mu = beta N^gamma / N: the transmission that leaves N_out = beta N^gamma of the
+    N input photons (Results)."""
+    N, beta, gamma = np.broadcast_arrays(np.asarray(N, dtype=np.float64), np.asarray(beta, dtype=np.float64),
+                                         np.asarray(gamma, dtype=np.float64))
+    mu = beta * N ** gamma / N
+    if np.any(mu > 1.0) or np.any(mu < 0.0):
+        raise ValueError("beta N^gamma / N must lie in [0, 1]")
+    return mu
+
+
+def asymptotic_ee(N, beta, gamma, r: float = 0.88, n_max: int = 8, alpha: Optional[float] = None) -> Dict[str, np.ndarray]:
+    """App. C estimate of the system's operator EE for every (N, beta, gamma) of the
+    broadcast inputs: mu = beta N^gamma / N, theta = pi / 4, S_system = N S_mode.
+    Returns ``{"mu": ..., "S1": ..., "S_alpha": ... or None}`` with the inputs' shape.
+    Every mode entropy is computed by the library's kernels in one batch."""
+    mu = transmission(N, beta, gamma)
+    N = np.broadcast_to(np.asarray(N, dtype=np.float64), mu.shape)
+    res = _mpo.asymptotic_ee(np.full(mu.size, float(r)), mu.ravel(), np.full(mu.size, math.pi / 4), n_max, alpha)
+    out = {"mu": mu, "S1": (N.ravel() * res["S1"]).reshape(mu.shape), "S_alpha": None}
+    if alpha is not None:
+        out["S_alpha"] = (N.ravel() * res["S_alpha"]).reshape(mu.shape)
+    return out
+
+
+def n_max_convergence(N: int = 50, beta: float = 1.0, gamma: float = 0.5, r: float = 0.88,
+                      n_maxes: Sequence[int] = tuple(range(2, 17))) -> List[tuple]:
+    """[(n_max, N S)] for increasing photon cutoffs (Fig. 1(d))."""
+    return [(int(n), float(asymptotic_ee(N, beta, gamma, r, int(n))["S1"])) for n in n_maxes]

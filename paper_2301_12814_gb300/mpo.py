@@ -26,7 +26,9 @@ EXPORTS = [
     "mpo_plan_destroy",
     "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
+    "mpo_asymptotic_ee", "mpo_asymptotic_ee_device",
 ]
+ASYM_NMAX = 23  # MPO_ASYM_NMAX
 
 
 class MPOError(RuntimeError):
@@ -71,6 +73,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp, _dp]),
         "mpo_plan_stage_times": (_i, [_p, _dp]),
         "mpo_svd_cluster_shape": (_i, [_ip, _ip, _ip, _ip]),
+        "mpo_asymptotic_ee": (_i, [_i, _i, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _i]),
+        "mpo_asymptotic_ee_device": (_i, [_i, _i, _p, _p, _p, ctypes.c_double, _p, _p, _p, _i, _p, _p]),
         "mpo_plan_destroy": (None, [_p]),
         "mpo_observables": (_i, [_p, _dp, _dp, _dp, _i]),
         "mpo_truncated_probability": (_i, [_p, _dp]),
@@ -112,6 +116,37 @@ def svd_cluster_shape() -> dict:
     v = np.zeros(4, dtype=np.int32)
     _check(_lib().mpo_svd_cluster_shape(*[v[i:].ctypes.data_as(_ip) for i in range(4)]), "mpo_svd_cluster_shape")
     return {"cluster_size": int(v[0]), "clusters_fp64": int(v[1]), "clusters_fp32": int(v[2]), "min_n": int(v[3])}
+
+
+def asymptotic_ee(r, mu, theta, n_max: int, alpha: Optional[float] = None, spectrum: bool = False) -> dict:
+    """App. C estimator for a batch of points (mpo_asymptotic_ee): one squeezed mode of
+    squeezing r, transmission mu, split angle theta, cut at n_max photons.  Returns
+    ``{"S1": [npts], "S_alpha": [npts] or None, "spectrum": [npts, (n_max+1)^2] or None}``."""
+    r, mu, theta = (np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64))) for x in (r, mu, theta))
+    r, mu, theta = (np.ascontiguousarray(x) for x in np.broadcast_arrays(r, mu, theta))
+    n = r.size
+    K = (int(n_max) + 1) ** 2
+    S1 = np.zeros(n)
+    Sa = np.zeros(n) if alpha is not None else None
+    sp = np.zeros((n, K)) if spectrum else None
+    _check(_lib().mpo_asymptotic_ee(n, int(n_max), _d(r), _d(mu), _d(theta),
+                                    float(alpha) if alpha is not None else 0.0, _d(S1), _d(Sa), _d(sp), K),
+           "mpo_asymptotic_ee")
+    return {"S1": S1, "S_alpha": Sa, "spectrum": sp}
+
+
+def asymptotic_ee_device(r, mu, theta, n_max: int, S1, spectrum, alpha: Optional[float] = None, S_alpha=None,
+                         sweeps=None, stream=None) -> None:
+    """mpo_asymptotic_ee_device on caller-owned device buffers (objects exposing
+    ``data_ptr()``, e.g. torch CUDA tensors of float64; ``sweeps`` int32).  Asynchronous
+    on ``stream`` (an object with ``cuda_stream`` or a raw handle; None = default)."""
+    n = int(r.numel())
+    K = (int(n_max) + 1) ** 2
+    ptr = (lambda t: None if t is None else t.data_ptr())
+    sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(_lib().mpo_asymptotic_ee_device(n, int(n_max), ptr(r), ptr(mu), ptr(theta),
+                                           float(alpha) if alpha is not None else 0.0, ptr(S1), ptr(S_alpha),
+                                           ptr(spectrum), K, ptr(sweeps), sp), "mpo_asymptotic_ee_device")
 
 
 class Plan:

@@ -74,3 +74,25 @@ def test_no_gpu_is_reported_not_faked(lib):
     with pytest.raises(MPOError) as ei:
         MPO(4, 4, [0.5] * 4, [0.5] * 4)
     assert ei.value.status == 9
+    from paper_2301_12814_gb300 import mpo
+    with pytest.raises(MPOError) as ei:
+        mpo.asymptotic_ee([0.88], [0.3], [0.7853981633974483], 8)
+    assert ei.value.status == 9
+
+
+def test_asymptotic_argument_checks(lib):
+    """mpo_asymptotic_ee validates sizes and ranges on the host before any CUDA call."""
+    from paper_2301_12814_gb300 import mpo
+    one = np.array([0.5]); K = 81
+    out = np.zeros(1); sp = np.zeros(K)
+    call = lambda n, r, mu, th, alpha=0.0, Sa=None, ld=K: lib.mpo_asymptotic_ee(
+        1, n, mpo._d(r), mpo._d(mu), mpo._d(th), alpha, mpo._d(out), mpo._d(Sa), mpo._d(sp), ld)
+    assert call(0, one, one, one) == 1
+    assert call(24, one, one, one) == 1
+    assert call(8, np.array([3.5]), one, one) == 1
+    assert call(8, one, np.array([1.01]), one) == 1
+    assert call(8, one, one, np.array([np.inf])) == 1
+    assert call(8, one, one, one, alpha=0.0, Sa=np.zeros(1)) == 1
+    assert call(8, one, one, one, ld=80) == 1
+    assert lib.mpo_asymptotic_ee(0, 8, None, None, None, 0.0, None, None, None, 0) == 0
+    assert lib.mpo_asymptotic_ee_device(1, 8, None, None, None, 0.0, None, None, None, K, None, None) == 1
