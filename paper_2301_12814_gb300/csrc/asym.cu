@@ -63,10 +63,10 @@ __host__ __device__ inline AsymSmem asym_smem(int n) {
   const size_t L = (size_t)n + 1;
   AsymSmem s;
   s.a = 0;
-  s.rho = asym_align(s.a + (size_t)nb0 * nb0 * sizeof(double));
+  s.rho = asym_align(s.a + (size_t)nb0 * (nb0 | 1) * sizeof(double));  // odd column stride
   s.v = asym_align(s.rho + L * L * sizeof(double));
   s.tab = asym_align(s.v + L * L * sizeof(double));  // binomials, then Kraus factors
-  s.pairs = asym_align(s.tab + 2 * L * L * sizeof(double) + 2 * L * sizeof(double));
+  s.pairs = asym_align(s.tab + 2 * L * L * sizeof(double) + 5 * L * sizeof(double));
   s.total = asym_align(s.pairs + (size_t)nb0 * sizeof(int) + 64);
   return s;
 }
@@ -90,27 +90,40 @@ __device__ inline void asym_pair(int nbe, int k, int i, int& p, int& q) {
   }
 }
 
-// grid: 4 * npts CTAs; item = 4 * point + block.  Writes the block's squared singular
-// values to spec[point * ld + off[block] + j] and its sweep count to sweeps[item].
+// CTA width for photon cutoff n: one warp per 32 column pairs of the largest block
+// (one warp up to n = 12, three at n = 23).
+__host__ __device__ inline int asym_threads(int n) {
+  int nb0, off0;
+  asym_block_of(n, 0, nb0, off0);
+  const int pairs = (nb0 + 1) / 2;
+  int w = (pairs + 31) / 32;
+  return 32 * (w < 1 ? 1 : (w > ASYM_WARPS ? ASYM_WARPS : w));
+}
+
+// grid: 4 * npts CTAs of asym_threads(n) threads; item = 4 * point + block.  Writes the
+// block's squared singular values to spec[point * ld + off[block] + j] and its sweep
+// count to sweeps[item].
 __global__ void __launch_bounds__(ASYM_THREADS)
 k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __restrict__ mu_all,
              const double* __restrict__ th_all, double* __restrict__ spec, int ld, int* __restrict__ sweeps) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int item = blockIdx.x, pt = item >> 2, sec = item & 3;
   if (pt >= npts) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, nth = blockDim.x;
   const int L = n + 1;
   int nb, boff;
   asym_block_of(n, sec, nb, boff);
+  const int lda = nb | 1;  // odd column stride: lanes on different columns hit different banks
   const AsymSmem lay = asym_smem(n);
-  double* A = (double*)(smem + lay.a);      // [nb][nb], column b at A + b * nb
+  double* A = (double*)(smem + lay.a);      // column b at A + b * lda, rows 0..nb-1
   double* rho = (double*)(smem + lay.rho);  // [L][L] rho_lossy
   double* V = (double*)(smem + lay.v);      // [L][L] <k_u, k_d|U|k_u + k_d>
   double* bin = (double*)(smem + lay.tab);  // [L][L] C(a, b)
   double* kr = bin + L * L;                 // [L][L] Kraus factor K^(l)[o, o + l] at [o][l]
-  double* psi = kr + L * L;                 // [L]
-  double* pw = psi + L;                     // [L] scratch
+  double* psi = kr + L * L;                 // [L] squeezed amplitudes
+  double* pw = psi + L;                     // [4][L] mu^o, (1-mu)^l, cos^k, sin^k
   int* pairs = (int*)(smem + lay.pairs);    // [nb] packed (k | k' << 8)
+  __shared__ double s_red[ASYM_WARPS];
 
   const double r = r_all[pt], mu = mu_all[pt], th = th_all[pt];
   if (nb == 0) {
@@ -118,24 +131,21 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
     return;
   }
 
-  // 1. tables: Pascal's triangle, squeezed amplitudes (App. C), Kraus factors (Eq. `lossy`),
-  //    split amplitudes (Eq. `kun`), pair list of this block
+  // 1. tables: squeezed amplitudes (App. C), powers for the Kraus factors (Eq. `lossy`)
+  //    and the split (Eq. `kun`), exact binomials, pair list of this block
   if (tid == 0) {
-    for (int a = 0; a < L; ++a)
-      for (int b = 0; b < L; ++b) bin[a * L + b] = (b == 0) ? 1.0 : (b > a ? 0.0 : bin[(a - 1) * L + b - 1] + (b < a ? bin[(a - 1) * L + b] : 0.0));
     const double t = -tanh(r);
     psi[0] = 1.0 / sqrt(cosh(r));
     for (int k = 1; k < L; ++k) psi[k] = (k & 1) ? 0.0 : psi[k - 2] * t * sqrt((double)(k - 1) / (double)k);
-    // pw[o] = mu^o; the loss factor (1 - mu)^l is accumulated per row below
-    pw[0] = 1.0;
-    for (int o = 1; o < L; ++o) pw[o] = pw[o - 1] * mu;
-    for (int o = 0; o < L; ++o) {
-      double lf = 1.0;
-      for (int l = 0; o + l < L; ++l) {
-        kr[o * L + l] = sqrt(bin[(o + l) * L + o] * pw[o] * lf);
-        lf *= (1.0 - mu);
-      }
+  } else if (tid == 1 % nth) {
+    const double cth = cos(th), sth = sin(th);
+    double a = 1.0, b = 1.0, c = 1.0, d = 1.0;
+    for (int k = 0; k < L; ++k) {
+      pw[k] = a; pw[L + k] = b; pw[2 * L + k] = c; pw[3 * L + k] = d;
+      a *= mu; b *= (1.0 - mu); c *= cth; d *= sth;
     }
+  }
+  if (tid == (2 % nth)) {
     int cnt = 0;
     const bool sym = sec < 2;
     const int par = sec & 1;
@@ -143,9 +153,23 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
       for (int u2 = sym ? u : u + 1; u2 < L; ++u2)
         if (((u + u2) & 1) == par) pairs[cnt++] = u | (u2 << 8);
   }
+  for (int idx = tid; idx < L * L; idx += nth) {
+    const int a = idx / L, b = idx % L;
+    long long c = 0;
+    if (b <= a) {
+      c = 1;
+      for (int i = 1; i <= b; ++i) c = c * (a - b + i) / i;  // exact: C(a-b+i, i) at every step
+    }
+    bin[idx] = (double)c;
+  }
   __syncthreads();
-  const double cth = cos(th), sth = sin(th);
-  for (int idx = tid; idx < L * L; idx += ASYM_THREADS) {
+  for (int idx = tid; idx < L * L; idx += nth) {
+    const int o = idx / L, l = idx % L;
+    kr[idx] = (o + l < L) ? sqrt(bin[(o + l) * L + o] * pw[o] * pw[L + l]) : 0.0;
+    V[idx] = (o + l < L) ? sqrt(bin[(o + l) * L + o]) * pw[2 * L + o] * pw[3 * L + l] : 0.0;  // V[k_u][k_d]
+  }
+  __syncthreads();
+  for (int idx = tid; idx < L * L; idx += nth) {
     const int m = idx / L, m2 = idx % L;
     double acc = 0.0;
     if (((m + m2) & 1) == 0) {
@@ -153,15 +177,6 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
       for (int l = 0; l <= lmax; ++l) acc += kr[m * L + l] * psi[m + l] * psi[m2 + l] * kr[m2 * L + l];
     }
     rho[idx] = acc;
-    // V[ku][kd]
-    const int ku = m, kd = m2;
-    double v = 0.0;
-    if (ku + kd < L) {
-      v = sqrt(bin[(ku + kd) * L + ku]);
-      for (int i = 0; i < ku; ++i) v *= cth;
-      for (int i = 0; i < kd; ++i) v *= sth;
-    }
-    V[idx] = v;
   }
   __syncthreads();
 
@@ -169,7 +184,8 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
   const bool sym = sec < 2;
 #define ASYM_F(u, u2, d, d2) \
   (((u) + (d) > n || (u2) + (d2) > n) ? 0.0 : V[(u) * L + (d)] * V[(u2) * L + (d2)] * rho[((u) + (d)) * L + ((u2) + (d2))])
-  for (int idx = tid; idx < nb * nb; idx += ASYM_THREADS) {
+  double f2 = 0.0;
+  for (int idx = tid; idx < nb * nb; idx += nth) {
     const int b = idx / nb, a = idx % nb;
     const int pa = pairs[a], pb = pairs[b];
     const int u = pa & 255, u2 = pa >> 8, d = pb & 255, d2 = pb >> 8;
@@ -182,52 +198,61 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
     } else {
       x = ASYM_F(u, u2, d, d2) - ASYM_F(u, u2, d2, d);
     }
-    A[(size_t)b * nb + a] = x;
+    A[b * lda + a] = x;
+    f2 = fma(x, x, f2);
   }
 #undef ASYM_F
-  __syncthreads();
-
-  // 3. one-sided Jacobi over the columns: warps take disjoint pairs of a round
-  __shared__ double s_red[ASYM_WARPS];
-  {
-    double f2 = 0.0;
-    for (int idx = tid; idx < nb * nb; idx += ASYM_THREADS) f2 = fma(A[idx], A[idx], f2);
-    f2 = warp_sum(f2);
-    if (lane == 0) s_red[warp] = f2;
-  }
+  f2 = warp_sum(f2);
+  if ((tid & 31) == 0) s_red[tid >> 5] = f2;
   __syncthreads();
   double frob2 = 0.0;
-  for (int w = 0; w < ASYM_WARPS; ++w) frob2 += s_red[w];
+  for (int w = 0; w < nth / 32; ++w) frob2 += s_red[w];
   const double gfloor = ASYM_FLOOR * frob2;
-  const int nbe = nb + (nb & 1);
+
+  // 3. one-sided Jacobi over the columns.  Each column pair of a round goes to a group
+  //    of g lanes (g a power of two, as large as the CTA allows) that split the rows;
+  //    the xor butterfly leaves bitwise identical sums in every lane of a group, so the
+  //    group agrees on the rotation.  Every lane runs the same number of slots, so the
+  //    full-mask shuffles always see the whole warp.
+  const int nbe = nb + (nb & 1), P = nbe / 2;
+  int g = 1;
+  while (g < 32 && 2 * g * P <= nth) g *= 2;
+  int gsh = 0;
+  while ((1 << gsh) < g) ++gsh;
+  const int slot = tid >> gsh, sub = tid & (g - 1), nslots = nth >> gsh;
   int sw = 0;
   for (; sw < ASYM_MAX_SWEEPS; ++sw) {
     int rotated = 0;
     for (int k = 0; k < nbe - 1; ++k) {
-      for (int i = warp; i < nbe / 2; i += ASYM_WARPS) {
-        int p, q;
-        asym_pair(nbe, k, i, p, q);
-        if (p >= nb || q >= nb) continue;
-        double* ap = A + (size_t)p * nb;
-        double* aq = A + (size_t)q * nb;
+      for (int base = 0; base < P; base += nslots) {
+        const int i = base + slot;
+        int p = 0, q = 0;
+        if (i < P) asym_pair(nbe, k, i, p, q);
+        const bool act = i < P && p < nb && q < nb;
+        double* ap = A + p * lda;
+        double* aq = A + q * lda;
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int e = lane; e < nb; e += 32) {
-          const double x = ap[e], y = aq[e];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (fabs(ga) > gfloor && fabs(ga) > ASYM_TOL * sqrt(al) * sqrt(be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          for (int e = lane; e < nb; e += 32) {
+        if (act) {
+          for (int e = sub; e < nb; e += g) {
             const double x = ap[e], y = aq[e];
-            ap[e] = c * x - s * y;
-            aq[e] = s * x + c * y;
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (act && fabs(ga) > gfloor && fabs(ga) > ASYM_TOL * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          const double c = rsqrt(fma(t, t, 1.0)), s = c * t;
+          for (int e = sub; e < nb; e += g) {
+            const double x = ap[e], y = aq[e];
+            ap[e] = fma(c, x, -s * y);
+            aq[e] = fma(s, x, c * y);
           }
           rotated = 1;
         }
@@ -238,12 +263,11 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
   }
 
   // 4. squared column norms = squared singular values of the block
-  for (int b = warp; b < nb; b += ASYM_WARPS) {
-    const double* ab = A + (size_t)b * nb;
+  for (int b = tid; b < nb; b += nth) {
+    const double* ab = A + b * lda;
     double s2 = 0.0;
-    for (int e = lane; e < nb; e += 32) s2 = fma(ab[e], ab[e], s2);
-    s2 = warp_sum(s2);
-    if (lane == 0) spec[(size_t)pt * ld + boff + b] = s2;
+    for (int e = 0; e < nb; ++e) s2 = fma(ab[e], ab[e], s2);
+    spec[(size_t)pt * ld + boff + b] = s2;
   }
   if (tid == 0 && sweeps) sweeps[item] = sw + 1;
 }
@@ -333,7 +357,7 @@ extern "C" mpo_status mpo_asymptotic_ee_device(int npts, int n_max, const double
   e = cudaFuncSetAttribute(k_asym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return asym_cuda(e);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  k_asym_block<<<npts * 4, ASYM_THREADS, smem, st>>>(npts, n_max, r, mu, theta, spectrum, ld, sweeps);
+  k_asym_block<<<npts * 4, asym_threads(n_max), smem, st>>>(npts, n_max, r, mu, theta, spectrum, ld, sweeps);
   k_asym_finalize<<<npts, ASYM_THREADS, 0, st>>>(npts, n_max, alpha, S_alpha ? 1 : 0, spectrum, ld, S1,
                                                  S_alpha);
   return asym_cuda(cudaGetLastError());
