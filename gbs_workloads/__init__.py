@@ -11,6 +11,10 @@ inputs both sides consume:
 * the workload recipes (M, d, chi, r, eta, seeds) of the five standard workloads
   and the per-instance draws of the batched one;
 * a greedy layering of the gate list into layers of gates on disjoint mode pairs;
+* a direct-dialled rectangular mesh (Russell et al., New J. Phys. 19, 033007 (2017)):
+  the same M-layer layout with every beam-splitter angle and phase drawn
+  independently from position-dependent laws that make the product Haar-random,
+  with no matrix drawn or decomposed;
 * the parameter grid of the asymptotic-entanglement sweep (Results, Fig. 1): numbers
   N of squeezed inputs, surviving-photon prefactors beta and exponents gamma.
 
@@ -34,7 +38,7 @@ import numpy as np
 __all__ = [
     "haar_unitary", "clements", "mesh_unitary", "gate_block", "Mesh",
     "Workload", "workload", "WORKLOADS", "layer_schedule", "batched_instances", "AsymptoticGrid",
-    "asymptotic_grid",
+    "asymptotic_grid", "elimination_steps", "dialled_mesh",
 ]
 
 
@@ -136,6 +140,46 @@ def clements(U: np.ndarray) -> Mesh:
     return Mesh(N, k, theta, phi, np.angle(d).astype(np.float64))
 
 
+def elimination_steps(N: int) -> List[Tuple[int, str, int, int]]:
+    """(mode n, side, diagonal i, position p) of every nulling step of ``clements`` in
+    its order: side 'R' = column operation (right factor), 'L' = row operation."""
+    steps = []
+    for i in range(N - 1):
+        if i % 2 == 0:
+            for j in range(i + 1):
+                steps.append((i - j, "R", i, j))
+        else:
+            for j in range(1, i + 2):
+                steps.append((N + j - i - 3, "L", i, j - 1))
+    return steps
+
+
+def dialled_mesh(M: int, seed: int) -> Mesh:
+    """A Haar-random M-layer rectangular mesh dialled gate by gate.
+
+    For a Haar-random U the nulling step at position p of diagonal i of ``clements``
+    has sin^2(theta) ~ Beta(a, 1) with a = min(2p + 1, 2(i + 1 - p)), independently of
+    every other step, and every phase (gate phases, final screen) is uniform on
+    [0, 2 pi).  So theta = asin(xi^(1 / 2a)) with xi uniform on [0, 1] (the inverse of
+    the Beta(a, 1) CDF x^a).  The gates come out in ``clements``' layout and order, so
+    the mesh is interchangeable with ``clements(haar_unitary(M, seed))``.  Draws
+    (numpy default_rng(seed)): per step in elimination order xi then phi, then the M
+    final phases."""
+    rng = np.random.default_rng(seed)
+    right: List[Tuple[int, float, float]] = []
+    left: List[Tuple[int, float, float]] = []
+    for n, side, i, p in elimination_steps(M):
+        a = min(2 * p + 1, 2 * (i + 1 - p))
+        xi = rng.uniform()
+        th = math.asin(min(1.0, xi ** (1.0 / (2 * a))))
+        ph = rng.uniform(0.0, 2 * math.pi)
+        (right if side == "R" else left).append((n, th, ph))
+    order = right + list(reversed(left))
+    final = rng.uniform(0.0, 2 * math.pi, M)
+    return Mesh(M, np.array([g[0] for g in order], dtype=np.int32), np.array([g[1] for g in order]),
+                np.array([g[2] for g in order]), final)
+
+
 def mesh_unitary(mesh: Mesh) -> np.ndarray:
     """Rebuild D T_L ... T_1 from a mesh (used to check a decomposition)."""
     V = np.eye(mesh.M, dtype=np.complex128)
@@ -177,7 +221,11 @@ class Workload:
     def n_cap(self) -> int:
         return self.d - 1
 
-    def mesh(self, i: int = 0) -> Mesh:
+    def mesh(self, i: int = 0, dialled: bool = False) -> Mesh:
+        """Instance i's mesh: the Clements decomposition of haar_unitary(M, seed), or
+        with ``dialled`` the direct-dialled mesh of the same seed (another unitary)."""
+        if dialled:
+            return dialled_mesh(self.M, self.seeds[i])
         return clements(haar_unitary(self.M, self.seeds[i]))
 
     def unitary(self, i: int = 0) -> np.ndarray:

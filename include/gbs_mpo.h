@@ -30,6 +30,8 @@
 #ifndef GBS_MPO_H
 #define GBS_MPO_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -193,6 +195,27 @@ mpo_status mpo_operator_entropy(mpo_handle h, double* S, double* purity,
  * lam [(M+1)*ld] and charge [(M+1)*ld*2] (c, cbar per index), row b holding bond
  * b's chi[b] entries; either may be NULL.  ld >= largest chi.  Synchronises. */
 mpo_status mpo_get_bonds(mpo_handle h, int inst, int ld, int* chi, double* lam, int* charge);
+
+/* Checkpoints (no counterpart in the paper: restart support for long meshes).
+ * A checkpoint is a host byte buffer: a 128-byte header (magic "GBSMPOCK", format
+ * version, M, d, n_cap, batch, charge-pair count, bond capacity D, precision, the
+ * caller's gate cursor, an FNV-1a checksum of the payload), then the handle's device
+ * state image (bond dimensions, charges, segment offsets, lambda, entropies, Gamma)
+ * and the per-instance kept probability.  The image is the library's own layout: a
+ * checkpoint loads only into a handle of the same M, d, n_cap, batch, D and precision
+ * (chi caps may differ) from the same library version.
+ *   mpo_checkpoint_bytes  *bytes = the buffer size a checkpoint of h needs.
+ *   mpo_save   copies the current state into buf (host, >= that size) with the
+ *              caller's gate cursor (for example the number of gates applied);
+ *              synchronises; device errors first poison the handle as usual.
+ *   mpo_load   replaces the state of h by the checkpoint; *cursor (nullable)
+ *              receives the saved cursor.  MPO_ERR_ARG for a short buffer, a wrong
+ *              magic or version, a shape mismatch or a checksum mismatch (the state
+ *              is then unchanged).  mpo_reset still returns to the initial state.
+ *              Synchronises. */
+mpo_status mpo_checkpoint_bytes(mpo_handle h, size_t* bytes);
+mpo_status mpo_save(mpo_handle h, void* buf, size_t bytes, long long cursor);
+mpo_status mpo_load(mpo_handle h, const void* buf, size_t bytes, long long* cursor);
 
 /* Device pointers/sizes for callers that manage their own buffers: the bond
  * capacity D (Gamma matrices are D x D) and the number of instances. */

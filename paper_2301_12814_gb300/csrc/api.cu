@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -699,6 +700,84 @@ mpo_status mpo_get_bonds(mpo_handle h, int inst, int ld, int* chi, double* lam, 
 }
 
 int mpo_bond_capacity(mpo_handle h) { return h ? h->D : 0; }
+
+// ---------------------------------------------------------------- checkpoints
+// Layout: CkptHeader (128 bytes) | device state image (state_bytes) | kept [B] doubles.
+// The state image is the handle's own device layout, so a checkpoint is only valid for
+// a handle of the same shape (M, d, n_cap, batch, D, precision) built by this library.
+namespace {
+constexpr char kCkptMagic[8] = {'G', 'B', 'S', 'M', 'P', 'O', 'C', 'K'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int32_t M, d, ncap, B, P, D, prec, reserved0;
+  uint64_t state_bytes, cursor, checksum;
+  uint8_t reserved[128 - 8 - 8 - 32 - 24];
+};
+static_assert(sizeof(CkptHeader) == 128, "checkpoint header is 128 bytes");
+
+// FNV-1a, 64 bit (Fowler, Noll, Vo): detects torn or corrupted buffers, not tampering
+uint64_t fnv1a(const unsigned char* p, size_t n, uint64_t hsh = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) {
+    hsh ^= p[i];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+
+size_t ckpt_bytes(const mpo_ctx* h) { return sizeof(CkptHeader) + h->state_bytes + (size_t)h->B * sizeof(double); }
+}  // namespace
+
+mpo_status mpo_checkpoint_bytes(mpo_handle h, size_t* bytes) {
+  if (!h || !bytes) return MPO_ERR_ARG;
+  *bytes = ckpt_bytes(h);
+  return MPO_OK;
+}
+
+mpo_status mpo_save(mpo_handle h, void* buf, size_t bytes, long long cursor) {
+  if (!h || !buf) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  if (bytes < ckpt_bytes(h)) return MPO_ERR_ARG;
+  unsigned char* out = (unsigned char*)buf;
+  unsigned char* img = out + sizeof(CkptHeader);
+  CK(cudaMemcpyAsync(img, h->state, h->state_bytes, cudaMemcpyDeviceToHost, h->stream));
+  mpo_status st = poll_error(h);
+  if (st != MPO_OK) return st;
+  std::memcpy(img + h->state_bytes, h->kept.data(), (size_t)h->B * sizeof(double));
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.header_bytes = sizeof(CkptHeader);
+  hd.M = h->M; hd.d = h->d; hd.ncap = h->ncap; hd.B = h->B; hd.P = h->P; hd.D = h->D; hd.prec = h->prec;
+  hd.state_bytes = h->state_bytes;
+  hd.cursor = (uint64_t)cursor;
+  hd.checksum = fnv1a(img, h->state_bytes + (size_t)h->B * sizeof(double));
+  std::memcpy(out, &hd, sizeof(hd));
+  return MPO_OK;
+}
+
+mpo_status mpo_load(mpo_handle h, const void* buf, size_t bytes, long long* cursor) {
+  if (!h || !buf) return MPO_ERR_ARG;
+  if (h->poisoned) return MPO_ERR_POISONED;
+  if (bytes < sizeof(CkptHeader)) return MPO_ERR_ARG;
+  CkptHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion || hd.header_bytes != sizeof(CkptHeader))
+    return MPO_ERR_ARG;
+  if (hd.M != h->M || hd.d != h->d || hd.ncap != h->ncap || hd.B != h->B || hd.P != h->P || hd.D != h->D ||
+      hd.prec != h->prec || hd.state_bytes != h->state_bytes || bytes < ckpt_bytes(h))
+    return MPO_ERR_ARG;
+  const unsigned char* img = (const unsigned char*)buf + sizeof(CkptHeader);
+  if (fnv1a(img, h->state_bytes + (size_t)h->B * sizeof(double)) != hd.checksum) return MPO_ERR_ARG;
+  CK(cudaMemcpyAsync(h->state, img, h->state_bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(h->kept.data(), img + h->state_bytes, (size_t)h->B * sizeof(double));
+  if (cursor) *cursor = (long long)hd.cursor;
+  return MPO_OK;
+}
 
 mpo_status mpo_sync(mpo_handle h) {
   if (!h) return MPO_ERR_ARG;

@@ -26,7 +26,7 @@ EXPORTS = [
     "mpo_plan_destroy",
     "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
-    "mpo_asymptotic_ee", "mpo_asymptotic_ee_device",
+    "mpo_asymptotic_ee", "mpo_asymptotic_ee_device", "mpo_checkpoint_bytes", "mpo_save", "mpo_load",
 ]
 ASYM_NMAX = 23  # MPO_ASYM_NMAX
 
@@ -73,6 +73,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_plan_profile": (_i, [_p, _dp, _ip, _dp, _dp]),
         "mpo_plan_stage_times": (_i, [_p, _dp]),
         "mpo_svd_cluster_shape": (_i, [_ip, _ip, _ip, _ip]),
+        "mpo_checkpoint_bytes": (_i, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+        "mpo_save": (_i, [_p, _p, ctypes.c_size_t, ctypes.c_longlong]),
+        "mpo_load": (_i, [_p, _p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_longlong)]),
         "mpo_asymptotic_ee": (_i, [_i, _i, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _i]),
         "mpo_asymptotic_ee_device": (_i, [_i, _i, _p, _p, _p, ctypes.c_double, _p, _p, _p, _i, _p, _p]),
         "mpo_plan_destroy": (None, [_p]),
@@ -272,6 +275,23 @@ class MPO:
         _check(_lib().mpo_observables(self._h, _d(tr), _d(n1), _d(n2), 1 if normalize else 0),
                "mpo_observables")
         return tr, n1.reshape(B, M), n2.reshape(B, M)
+
+    def save(self, cursor: int = 0) -> np.ndarray:
+        """Checkpoint of the current state (mpo_save) as a uint8 array; ``cursor`` is
+        stored with it (for example the number of gates applied so far)."""
+        n = ctypes.c_size_t()
+        _check(_lib().mpo_checkpoint_bytes(self._h, ctypes.byref(n)), "mpo_checkpoint_bytes")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(_lib().mpo_save(self._h, buf.ctypes.data_as(_p), n.value, int(cursor)), "mpo_save")
+        return buf
+
+    def load(self, buf) -> int:
+        """Replace the state by a checkpoint from ``save`` (mpo_load); returns its cursor."""
+        buf = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray))
+                                   else buf, dtype=np.uint8)
+        cur = ctypes.c_longlong()
+        _check(_lib().mpo_load(self._h, buf.ctypes.data_as(_p), buf.size, ctypes.byref(cur)), "mpo_load")
+        return int(cur.value)
 
     def truncated_probability(self) -> np.ndarray:
         """[batch] probability cut from the initial state by the local dimension d and

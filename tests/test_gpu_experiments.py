@@ -96,3 +96,25 @@ def test_choose_d_vs_oracle(ex):
         assert abs(tail - want) <= 1e-13, (d, tail, want)
     assert all(t >= 0.01 for d, t in res["visited"] if d < res["d"])
     assert res["visited"][-1][0] == res["d"]
+
+
+def test_dialled_mesh_vs_oracle(ex):
+    """A direct-dialled Haar mesh (the paper's M-layer array, App. A) through the whole
+    GPU path against the oracle on the same gates."""
+    from paper_2301_12814_gb300 import mpo
+    wl = w.workload("M16_d6_chi64")
+    mesh = wl.mesh(dialled=True)
+    G = mpo.MPO(wl.M, wl.d, wl.r[0], wl.eta[0], chi_max=wl.chi)
+    try:
+        disc = G.sweep_mesh([mesh.n_gates], mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
+        tr, n1, _ = G.observables()
+        S, _, _ = G.operator_entropy()
+    finally:
+        G.close()
+    P = u1mpo.U1MPO(wl.M, wl.d, wl.r[0], wl.eta[0], chi_max=wl.chi)
+    P.run_mesh(mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
+    ptr, pn1, _ = P.observables()
+    assert abs(tr[0] - ptr) <= 1e-10 * ptr
+    assert np.allclose(n1[0], pn1, rtol=1e-10, atol=1e-12)
+    assert np.allclose(S[0], np.asarray(P.entropy), rtol=1e-10, atol=1e-12)
+    assert np.allclose(disc, P.discarded, rtol=1e-10, atol=1e-12)

@@ -96,3 +96,11 @@ def test_asymptotic_argument_checks(lib):
     assert call(8, one, one, one, ld=80) == 1
     assert lib.mpo_asymptotic_ee(0, 8, None, None, None, 0.0, None, None, None, 0) == 0
     assert lib.mpo_asymptotic_ee_device(1, 8, None, None, None, 0.0, None, None, None, K, None, None) == 1
+
+
+def test_checkpoint_argument_checks(lib):
+    import ctypes as ct
+    n = ct.c_size_t()
+    assert lib.mpo_checkpoint_bytes(None, ct.byref(n)) == 1
+    assert lib.mpo_save(None, None, 0, 0) == 1
+    assert lib.mpo_load(None, None, 0, None) == 1
