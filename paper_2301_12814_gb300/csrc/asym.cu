@@ -22,6 +22,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/gbs_mpo.h"
@@ -100,15 +102,10 @@ __host__ __device__ inline int asym_threads(int n) {
   return 32 * (w < 1 ? 1 : (w > ASYM_WARPS ? ASYM_WARPS : w));
 }
 
-// grid: 4 * npts CTAs of asym_threads(n) threads; item = 4 * point + block.  Writes the
-// block's squared singular values to spec[point * ld + off[block] + j] and its sweep
-// count to sweeps[item].
-__global__ void __launch_bounds__(ASYM_THREADS)
-k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __restrict__ mu_all,
-             const double* __restrict__ th_all, double* __restrict__ spec, int ld, int* __restrict__ sweeps) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int item = blockIdx.x, pt = item >> 2, sec = item & 3;
-  if (pt >= npts) return;
+// One work item: block sec of point pt (the whole CTA).
+__device__ void asym_item(int sec, int pt, int n, const double* __restrict__ r_all,
+                          const double* __restrict__ mu_all, const double* __restrict__ th_all,
+                          double* __restrict__ spec, int ld, int* __restrict__ sweeps, unsigned char* smem) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int L = n + 1;
   int nb, boff;
@@ -126,6 +123,7 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
   __shared__ double s_red[ASYM_WARPS];
 
   const double r = r_all[pt], mu = mu_all[pt], th = th_all[pt];
+  const int item = 4 * pt + sec;
   if (nb == 0) {
     if (tid == 0 && sweeps) sweeps[item] = 0;
     return;
@@ -272,6 +270,24 @@ k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __
   if (tid == 0 && sweeps) sweeps[item] = sw + 1;
 }
 
+
+// grid: as many CTAs of asym_threads(n) threads as fit on the SMs, each looping over work items
+// f = blockIdx.x, blockIdx.x + gridDim.x, ...  Items are block-major (f = block * npts +
+// point), so the items a CTA takes -- and those of the CTAs sharing an SM -- mix the
+// four block sizes: with point-major items and a grid-wide stride divisible by 4 every
+// SM would see one block size only (3.8x more work on the SMs of the largest block at
+// n_max = 8).  Writes the block's squared singular values to
+// spec[point * ld + off[block] + j] and its sweep count to sweeps[4 * point + block].
+__global__ void __launch_bounds__(ASYM_THREADS)
+k_asym_block(int npts, int n, const double* __restrict__ r_all, const double* __restrict__ mu_all,
+             const double* __restrict__ th_all, double* __restrict__ spec, int ld, int* __restrict__ sweeps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (int f = blockIdx.x; f < 4 * npts; f += gridDim.x) {
+    asym_item(f / npts, f % npts, n, r_all, mu_all, th_all, spec, ld, sweeps, smem);
+    __syncthreads();  // shared memory is rebuilt by the next item
+  }
+}
+
 // grid: npts CTAs.  Normalises the pooled squared singular values of a point, writes
 // them back sorted in descending order, and the entropies (App. C, in bits).
 __global__ void __launch_bounds__(ASYM_THREADS)
@@ -332,6 +348,19 @@ k_asym_finalize(int npts, int n, double alpha, int want_alpha, double* __restric
   }
 }
 
+// Cap on resident CTAs per SM of k_asym_block; 0 (the default) = the occupancy limit.
+// GBS_MPO_ASYM_CTAS_PER_SM sets a cap.  At n_max = 8 (Fig. 1 grid, 768 points) the
+// occupancy limit (24) gave 3.67 ms, caps of 4 / 8 / 12 / 16 gave 5.91 / 4.08 / 3.91 /
+// 4.06 ms.
+int asym_ctas_per_sm() {
+  static int v = [] {
+    const char* e = getenv("GBS_MPO_ASYM_CTAS_PER_SM");
+    const int x = e ? atoi(e) : 0;
+    return x > 0 ? x : 0;
+  }();
+  return v;
+}
+
 mpo_status asym_cuda(cudaError_t e) {
   if (e == cudaSuccess) return MPO_OK;
   if (e == cudaErrorMemoryAllocation) return MPO_ERR_OOM;
@@ -357,7 +386,16 @@ extern "C" mpo_status mpo_asymptotic_ee_device(int npts, int n_max, const double
   e = cudaFuncSetAttribute(k_asym_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return asym_cuda(e);
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  k_asym_block<<<npts * 4, asym_threads(n_max), smem, st>>>(npts, n_max, r, mu, theta, spectrum, ld, sweeps);
+  const int threads = asym_threads(n_max);
+  int nsm = 0, per_sm = 0;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_asym_block, threads, smem);
+  if (e != cudaSuccess) return asym_cuda(e);
+  if (per_sm < 1) return MPO_ERR_ARG;
+  const long long items = 4ll * npts;
+  const int cap = asym_ctas_per_sm();
+  const int grid = (int)std::min<long long>(items, (long long)nsm * (cap > 0 ? std::min(per_sm, cap) : per_sm));
+  k_asym_block<<<grid, threads, smem, st>>>(npts, n_max, r, mu, theta, spectrum, ld, sweeps);
   k_asym_finalize<<<npts, ASYM_THREADS, 0, st>>>(npts, n_max, alpha, S_alpha ? 1 : 0, spectrum, ld, S1,
                                                  S_alpha);
   return asym_cuda(cudaGetLastError());
