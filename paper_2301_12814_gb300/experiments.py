@@ -12,10 +12,15 @@ run and with which bond dimension.
   double while the error exceeds 0.02), then narrow the bracket by bisection a few
   more times (App. A: the bond dimension is refined a few more times).
 * ``choose_d``: the smallest local dimension d whose initial state loses less than a
-  threshold of the probability to the Fock and photon-number cut (App. A: d is chosen
-  so that under 1% is truncated; the left-most charge is the total photon number, so
-  the cap n_cap = d - 1 binds the whole register and d grows with r and with the
-  number of squeezed inputs).
+  threshold of the probability to the truncation (App. A: d is chosen so that under
+  1 % is truncated; the left-most charge is the total photon number, so the cap
+  n_cap = d - 1 on that total is what binds, and d grows with r and with the number
+  of squeezed inputs).  The input state is cut generously (32 photons per mode)
+  before loss, so the cap is the binding cut.
+* ``truncation_curve`` / ``fig4b``: 1 - Tr rho after the full mesh against the bond
+  dimension, every chi of the curve as one instance of a single batched handle (Fig.
+  4(b): (M, mu) = (10, 0.2), (15, 0.15), (20, 0.1), every mode squeezed at r = 0.88
+  so that mu M ~ 2 photons survive; d by the 1 % rule; a dialled M-layer mesh).
 * ``asymptotic_ee`` / ``n_max_convergence``: the App. C estimate N S(mu = beta N^gamma / N)
   behind Fig. 1 (EE against the number N of squeezed inputs for surviving photons
   N_out = beta N^gamma, r = 0.88, n_max = 8) and its convergence in the photon cutoff
@@ -55,7 +60,7 @@ def _layers(layer_of: Sequence[int]) -> List[np.ndarray]:
 
 def ee_over_depth(M: int, d: int, r, eta, chi: Optional[int], k: Sequence[int], theta: Sequence[float],
                   phi: Sequence[float], layer_of: Sequence[int], patience: int = 10,
-                  precision: str = "fp64") -> Dict[str, object]:
+                  precision: str = "fp64", n_cap: Optional[int] = None) -> Dict[str, object]:
     """Apply the gates layer by layer (``layer_of[g]`` = layer of gate g; gates of one
     layer act on disjoint mode pairs) and stop by the App. A rule.
 
@@ -65,7 +70,7 @@ def ee_over_depth(M: int, d: int, r, eta, chi: Optional[int], k: Sequence[int], 
     k = np.asarray(k, dtype=np.int32)
     theta = np.asarray(theta, dtype=np.float64)
     phi = np.asarray(phi, dtype=np.float64)
-    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision)
+    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision, n_cap=n_cap)
     try:
         max_ee: List[float] = []
         stopped = False
@@ -84,8 +89,8 @@ def ee_over_depth(M: int, d: int, r, eta, chi: Optional[int], k: Sequence[int], 
             "max_over_depth": max(max_ee) if max_ee else 0.0, "trace": float(tr)}
 
 
-def _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision) -> float:
-    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision)
+def _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision, n_cap=None) -> float:
+    G = _mpo.MPO(M, d, r, eta, chi_max=chi, precision=precision, n_cap=n_cap)
     try:
         G.sweep_mesh([len(k)], k, theta, phi, final_phase)
         return float(1.0 - G.observables(normalize=False)[0][0])
@@ -95,7 +100,8 @@ def _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision) 
 
 def bond_dimension_search(M: int, d: int, r, eta, k: Sequence[int], theta: Sequence[float],
                           phi: Sequence[float], final_phase=None, chi0: int = 8, target: float = 0.02,
-                          refine: int = 3, chi_limit: int = 4096, precision: str = "fp64") -> Dict[str, object]:
+                          refine: int = 3, chi_limit: int = 4096, precision: str = "fp64",
+                          n_cap: Optional[int] = None) -> Dict[str, object]:
     """The smallest bond dimension found whose full-mesh truncation error 1 - Tr rho is
     at most ``target``: double from ``chi0`` until the error is within the target, then
     bisect the last bracket ``refine`` times.  Returns ``{"chi": ..., "error": ...,
@@ -106,7 +112,7 @@ def bond_dimension_search(M: int, d: int, r, eta, k: Sequence[int], theta: Seque
     visited = []
 
     def err(chi):
-        e = _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision)
+        e = _truncation_error(M, d, r, eta, chi, k, theta, phi, final_phase, precision, n_cap)
         visited.append((chi, e))
         return e
 
@@ -132,23 +138,98 @@ def bond_dimension_search(M: int, d: int, r, eta, k: Sequence[int], theta: Seque
     return {"chi": hi, "error": e_hi, "visited": visited}
 
 
-def choose_d(M: int, r, eta, threshold: float = 0.01, d_min: int = 2, d_max: int = 16) -> Dict[str, object]:
-    """Scan d = d_min .. d_max and return the first whose truncated probability
-    (``MPO.truncated_probability``, the kernel-computed 1 - Tr(P_cap (x) rho_j P_cap)
-    with n_cap = d - 1) is below ``threshold``.  The kept set only grows with d, so the
-    first hit is the smallest.  Returns ``{"d": ..., "tail": ..., "visited":
-    [(d, tail), ...]}`` (``d`` is None if d_max is not enough)."""
+def truncation_curve(M: int, d: int, r, eta, k: Sequence[int], theta: Sequence[float], phi: Sequence[float],
+                     final_phase=None, chis: Sequence[int] = (8, 16, 32, 64, 128), precision: str = "fp64",
+                     n_cap: Optional[int] = None) -> List[tuple]:
+    """[(chi, 1 - Tr rho)] after the whole mesh for every chi in ``chis``; the curve is
+    one batched run (instance i capped at chis[i], all on the same mesh)."""
+    chis = [int(c) for c in chis]
+    B = len(chis)
+    k = np.tile(np.asarray(k, dtype=np.int32), B)
+    th = np.tile(np.asarray(theta, dtype=np.float64), B)
+    ph = np.tile(np.asarray(phi, dtype=np.float64), B)
+    fp = None if final_phase is None else np.tile(np.asarray(final_phase, dtype=np.float64), B)
+    n = len(k) // B
+    G = _mpo.MPO(M, d, r, eta, chi_max=chis, batch=B, precision=precision, n_cap=n_cap)
+    try:
+        G.sweep_mesh([n] * B, k, th, ph, fp)
+        tr = G.observables(normalize=False)[0]
+    finally:
+        G.close()
+    return [(c, float(1.0 - t)) for c, t in zip(chis, tr)]
+
+
+FIG4B = ((10, 0.2), (15, 0.15), (20, 0.1))
+
+
+def fig4b(seed: int = 0, r: float = 0.88, chi_max: int = 256, target: float = 0.02, refine: int = 3,
+          precision: str = "fp64", report=None) -> List[Dict[str, object]]:
+    """Fig. 4(b)'s three configurations on the dialled M-layer mesh of ``seed``: d by the
+    1 % rule, then App. A's chi search done as two batched runs -- the doubling phase
+    (chi = 8, 16, ..., chi_max in one handle) and the refinement (``refine`` evenly
+    spaced chi inside the first bracket that meets ``target``, in a second handle).
+    ``report`` (callable or None) receives each configuration's result when done."""
+    import gbs_workloads as w
+    out = []
+    for M, mu in FIG4B:
+        rr, ee = [r] * M, [mu] * M
+        dsel = choose_d(M, rr, ee)
+        if dsel["d"] is None:
+            raise ValueError(f"no d <= 16 truncates under 1% at M = {M}")
+        d, d_in, cap = dsel["d"], dsel["d_in"], dsel["n_cap"]
+        mesh = w.dialled_mesh(M, seed)
+        run = lambda chis: truncation_curve(M, d_in, rr, ee, mesh.k, mesh.theta, mesh.phi, mesh.final_phase,
+                                            chis, precision, n_cap=cap)
+        doubling = [8]
+        while doubling[-1] * 2 <= chi_max:
+            doubling.append(doubling[-1] * 2)
+        curve = run(doubling)
+        hit = next((i for i, (_, e) in enumerate(curve) if e <= target), None)
+        chi_t, err_t, refined = None, None, []
+        if hit is not None:
+            chi_t, err_t = curve[hit]
+            lo = curve[hit - 1][0] if hit > 0 else 0
+            step = (chi_t - lo) / (refine + 1)
+            mids = sorted({int(round(lo + step * (i + 1))) for i in range(refine)} - {lo, chi_t} - {0})
+            if mids:
+                refined = run(mids)
+                for c, e in refined:
+                    if e <= target and c < chi_t:
+                        chi_t, err_t = c, e
+                        break
+        res = {"M": M, "mu": mu, "d": d, "n_cap": cap, "d_in": d_in, "truncated": dsel["tail"], "curve": curve,
+               "refined": refined, "chi_for_target": chi_t, "error_at_chi": err_t}
+        if report is not None:
+            report(res)
+        out.append(res)
+    return out
+
+
+D_IN = 32  # input cutoff per mode (photons before loss) for the App. A choice of d; MPO_D_LOCAL_MAX
+
+
+def choose_d(M: int, r, eta, threshold: float = 0.01, d_min: int = 2, d_max: int = 16,
+             d_in: int = D_IN) -> Dict[str, object]:
+    """App. A's choice of d: the smallest local dimension d whose cap on the total
+    photon number, n_cap = d - 1 (the left-most charge), leaves less than ``threshold``
+    of the probability truncated.  Each mode's squeezed vacuum is cut at ``d_in``
+    photons before loss, so the cap is the binding truncation; the reported tail
+    (``MPO.truncated_probability``, computed by the kernels) includes both cuts.  The
+    kept set only grows with d, so the first hit is the smallest.  A run then uses
+    ``MPO(M, d_in, r, eta, n_cap=d - 1)``.  Returns ``{"d", "n_cap", "d_in", "tail",
+    "visited": [(d, tail), ...]}`` (``d`` is None if d_max is not enough)."""
     visited = []
     for d in range(int(d_min), int(d_max) + 1):
-        G = _mpo.MPO(M, d, r, eta, chi_max=1)
+        G = _mpo.MPO(M, d_in, r, eta, chi_max=1, n_cap=d - 1)
         try:
             tail = float(G.truncated_probability()[0])
         finally:
             G.close()
         visited.append((d, tail))
         if tail < threshold:
-            return {"d": d, "tail": tail, "visited": visited}
-    return {"d": None, "tail": visited[-1][1] if visited else None, "visited": visited}
+            return {"d": d, "n_cap": d - 1, "d_in": d_in, "tail": tail, "visited": visited}
+    return {"d": None, "n_cap": None, "d_in": d_in, "tail": visited[-1][1] if visited else None,
+            "visited": visited}
 
 
 def transmission(N, beta, gamma) -> np.ndarray:
@@ -180,3 +261,19 @@ def n_max_convergence(N: int = 50, beta: float = 1.0, gamma: float = 0.5, r: flo
                       n_maxes: Sequence[int] = tuple(range(2, 17))) -> List[tuple]:
     """[(n_max, N S)] for increasing photon cutoffs (Fig. 1(d))."""
     return [(int(n), float(asymptotic_ee(N, beta, gamma, r, int(n))["S1"])) for n in n_maxes]
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    import time
+    from . import build as _build
+    _mpo.load_library(_build.build())
+    if len(sys.argv) > 1 and sys.argv[1] == "fig4b":
+        t0 = time.perf_counter()
+        seed = int(sys.argv[2]) if len(sys.argv) > 2 else 0
+        chi_max = int(sys.argv[3]) if len(sys.argv) > 3 else 256
+        fig4b(seed=seed, chi_max=chi_max,
+              report=lambda res: print(json.dumps(dict(res, seconds=time.perf_counter() - t0)), flush=True))
+    else:
+        print("usage: python -m paper_2301_12814_gb300.experiments fig4b [seed]")

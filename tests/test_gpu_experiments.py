@@ -89,13 +89,33 @@ def test_choose_d_vs_oracle(ex):
     r = [0.9] * 2 + [0.0] * (M - 2)  # N = M / 4 squeezed inputs, as in App. A
     eta = [0.5] * M
     res = ex.choose_d(M, r, eta, threshold=0.01, d_min=4)
-    want_d = next(d for d in range(4, 17) if u1mpo.U1MPO(M, d, r, eta).truncated_probability < 0.01)
+    tail_of = lambda d: u1mpo.U1MPO(M, ex.D_IN, r, eta, n_cap=d - 1, chi_max=1).truncated_probability
+    want_d = next(d for d in range(4, 17) if tail_of(d) < 0.01)
     assert res["d"] == want_d and res["tail"] < 0.01
+    assert res["n_cap"] == want_d - 1 and res["d_in"] == ex.D_IN
     for d, tail in res["visited"]:
-        want = u1mpo.U1MPO(M, d, r, eta).truncated_probability
+        want = tail_of(d)
         assert abs(tail - want) <= 1e-13, (d, tail, want)
     assert all(t >= 0.01 for d, t in res["visited"] if d < res["d"])
     assert res["visited"][-1][0] == res["d"]
+
+
+def test_truncation_curve_vs_oracle(ex):
+    """1 - Tr rho against chi as one batched run (one instance per chi) equals separate
+    oracle runs, with the input cut above the cap (the choose_d setting)."""
+    M, cap = 8, 5
+    r = [0.88] * M
+    eta = [0.3] * M
+    mesh = w.dialled_mesh(M, 4)
+    curve = ex.truncation_curve(M, ex.D_IN, r, eta, mesh.k, mesh.theta, mesh.phi, mesh.final_phase,
+                                chis=(4, 8, 16, 32), n_cap=cap)
+    errs = [e for _, e in curve]
+    assert all(a >= b - 1e-12 for a, b in zip(errs, errs[1:]))  # more chi, less error
+    for chi, e in curve:
+        P = u1mpo.U1MPO(M, ex.D_IN, r, eta, chi_max=chi, n_cap=cap)
+        P.run_mesh(mesh.k, mesh.theta, mesh.phi, mesh.final_phase)
+        tr, _, _ = P.observables()
+        assert abs(e - (1.0 - tr)) <= 1e-10 * max(tr, 1e-300) + 1e-12, (chi, e, 1.0 - tr)
 
 
 def test_dialled_mesh_vs_oracle(ex):
