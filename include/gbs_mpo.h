@@ -77,6 +77,21 @@ typedef struct {
   void* cuda_stream;  /* cudaStream_t for all work of the handle; NULL = default    */
 } mpo_params;
 
+/* Device memory of handles and plans.  By default a handle's long-lived buffers come
+ * from cudaMalloc and per-call temporaries are stream-ordered (cudaMallocAsync on the
+ * handle's stream).  mpo_set_allocator installs a caller's pair instead -- for
+ * example one backed by a framework's caching allocator -- for every handle created
+ * afterwards; each handle keeps the pair it was created with and frees its memory
+ * through it.  alloc returns device memory of at least `bytes` bytes usable in
+ * stream order on `stream` (the handle's cudaStream_t), or NULL (the call then
+ * fails with MPO_ERR_OOM); free releases a pointer alloc returned, after the work the
+ * library queued on `stream`.  ctx is passed back unchanged.  NULL, NULL restores the
+ * CUDA runtime.  MPO_ERR_ARG if exactly one of the two is NULL.  The App. C entry
+ * points allocate through the CUDA runtime. */
+typedef void* (*mpo_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*mpo_free_fn)(void* ptr, void* stream, void* ctx);
+mpo_status mpo_set_allocator(mpo_alloc_fn alloc, mpo_free_fn free, void* ctx);
+
 /* Create a handle and build the initial state of every instance (App. B/C: each
  * mode starts as single-mode squeezed vacuum c_{2j} ~ (-tanh r)^j, truncated at d,
  * sent through a pure-loss channel of transmission eta; uniform loss commutes with

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -23,7 +24,19 @@ int svd_big_min();
 int svd_cluster_seed_max();
 int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32);
 
+// Device allocator of handles and plans: the CUDA runtime, or a caller's pair
+// installed by mpo_set_allocator (copied into each handle when it is created, so a
+// handle always frees with the functions that allocated its memory).
+struct DevAllocator {
+  mpo_alloc_fn alloc = nullptr;
+  mpo_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+DevAllocator g_allocator;
+std::mutex g_allocator_mu;
+
 struct mpo_ctx {
+  DevAllocator al;
   int M = 0, d = 0, ncap = 0, B = 0, P = 0, Pc = 0, D = 0;
   int prec = 0;
   cudaStream_t stream = nullptr;
@@ -72,6 +85,33 @@ struct mpo_plan_s {
 namespace {
 
 size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Long-lived buffers: cudaMalloc, or the caller's allocator on the handle's stream.
+cudaError_t dev_alloc(const mpo_ctx* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (h->al.alloc) {
+    *p = h->al.alloc(bytes, (void*)h->stream, h->al.ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+void dev_free(const mpo_ctx* h, void* p) {
+  if (!p) return;
+  if (h && h->al.free) h->al.free(p, (void*)h->stream, h->al.ctx);
+  else cudaFree(p);
+}
+// Per-call temporaries: stream-ordered (cudaMallocAsync on the handle's stream), or the
+// caller's allocator.
+cudaError_t tmp_alloc(const mpo_ctx* h, void** p, size_t bytes) {
+  *p = nullptr;
+  if (h->al.alloc) return dev_alloc(h, p, bytes);
+  return cudaMallocAsync(p, bytes, h->stream);
+}
+void tmp_free(const mpo_ctx* h, void* p) {
+  if (!p) return;
+  if (h->al.free) h->al.free(p, (void*)h->stream, h->al.ctx);
+  else cudaFreeAsync(p, h->stream);
+}
 
 mpo_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MPO_OK;
@@ -132,7 +172,7 @@ mpo_status poll_error(mpo_handle h) {
 
 mpo_status ensure_slots(mpo_handle h, int need) {
   if (need <= h->nslots) return MPO_OK;
-  if (h->ws_buf) { CK(cudaStreamSynchronize(h->stream)); CK(cudaFree(h->ws_buf)); h->ws_buf = nullptr; }
+  if (h->ws_buf) { CK(cudaStreamSynchronize(h->stream)); dev_free(h, h->ws_buf); h->ws_buf = nullptr; }
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
   w.big_min = svd_big_min();
@@ -169,7 +209,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_ls = take((size_t)S * w.Pc * sizeof(int));
   size_t o_ct = take(8 * sizeof(int));
   void* buf = nullptr;
-  CK(cudaMalloc(&buf, off));
+  CK(dev_alloc(h, &buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
   char* b = (char*)buf;
   w.blk = (int*)(b + o_blk); w.scal = (int*)(b + o_scal); w.rowoff = (int*)(b + o_ro);
@@ -275,6 +315,10 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count == 0) return MPO_ERR_NOT_BUILT;
   mpo_ctx* h = new (std::nothrow) mpo_ctx();
   if (!h) return MPO_ERR_OOM;
+  {
+    std::lock_guard<std::mutex> lk(g_allocator_mu);
+    h->al = g_allocator;
+  }
   h->M = M; h->d = d; h->ncap = ncap; h->B = B;
   h->P = (ncap + 1) * (ncap + 1);
   h->Pc = (ncap + 1) * (ncap + 2) / 2;
@@ -310,16 +354,16 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
   h->state_bytes = off;
   mpo_status st = MPO_OK;
   auto fail = [&](mpo_status s) { mpo_destroy(h); return s; };
-  if (cudaMalloc(&h->state, off) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&h->snap, off) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, &h->state, off) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, &h->snap, off) != cudaSuccess) return fail(MPO_ERR_OOM);
   if (cudaMemsetAsync(h->state, 0, off, h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
   char* sb = (char*)h->state;
   MpoDev& dv = h->dev;
   dv.B = B; dv.M = M; dv.ncap = ncap; dv.P = h->P; dv.D = (int)D;
   dv.chi = (int*)(sb + o_chi); dv.charge = (int*)(sb + o_ch); dv.segoff = (int*)(sb + o_seg);
   dv.lam = (double*)(sb + o_lam); dv.entropy = (double*)(sb + o_ent); dv.gam = (double2*)(sb + o_gam);
-  if (cudaMalloc(&h->d_err, 4 * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&h->d_chicap, B * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&h->d_err, 4 * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&h->d_chicap, B * sizeof(int)) != cudaSuccess) return fail(MPO_ERR_OOM);
   dv.err = h->d_err; dv.chi_cap = h->d_chicap;
   if (cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), h->stream) != cudaSuccess) return fail(MPO_ERR_CUDA);
   if (cudaMemcpyAsync(h->d_chicap, h->chicap.data(), B * sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
@@ -327,8 +371,8 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
   // init scratch
   const long long per = (long long)(M + 1) * h->P * 3 + (long long)M * h->P * 2 + 64;
   double* d_scr = nullptr; double* d_re = nullptr;
-  if (cudaMalloc(&d_scr, per * B * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&d_re, 2ll * B * M * sizeof(double)) != cudaSuccess) { cudaFree(d_scr); return fail(MPO_ERR_OOM); }
+  if (dev_alloc(h, (void**)&d_scr, per * B * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&d_re, 2ll * B * M * sizeof(double)) != cudaSuccess) { dev_free(h, d_scr); return fail(MPO_ERR_OOM); }
   cudaMemcpyAsync(d_re, r, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   cudaMemcpyAsync(d_re + (size_t)B * M, eta, (size_t)B * M * sizeof(double), cudaMemcpyHostToDevice, h->stream);
   launch_init(h->dev, d_re, d_re + (size_t)B * M, d, d_scr, h->stream);
@@ -340,7 +384,7 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
     e = cudaMemcpy2DAsync(h->kept.data(), sizeof(double), d_scr + (per - 64), per * sizeof(double),
                           sizeof(double), B, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(d_scr); cudaFree(d_re);
+  dev_free(h, d_scr); dev_free(h, d_re);
   if (e != cudaSuccess) return fail(cuda_status(e));
   if (gate_module_init() != cudaSuccess) return fail(MPO_ERR_CUDA);
   st = poll_error(h);
@@ -348,10 +392,10 @@ mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const d
   if (cudaMemcpyAsync(h->snap, h->state, off, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
     return fail(MPO_ERR_CUDA);
   // helpers
-  if (cudaMalloc(&h->d_gate1, sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&h->d_disc1, sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&h->d_obs_scratch, 2ll * B * (M + 1) * D * sizeof(double2)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&h->d_obs_out, (size_t)B * (1 + 2 * M + M + 1) * sizeof(double)) != cudaSuccess)
+  if (dev_alloc(h, (void**)&h->d_gate1, sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&h->d_disc1, sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&h->d_obs_scratch, 2ll * B * (M + 1) * D * sizeof(double2)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&h->d_obs_out, (size_t)B * (1 + 2 * M + M + 1) * sizeof(double)) != cudaSuccess)
     return fail(MPO_ERR_OOM);
   st = ensure_slots(h, 1);
   if (st != MPO_OK) return fail(st);
@@ -417,18 +461,18 @@ mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k, const 
   double* hdisc = (double*)(pb + align_up(ng * sizeof(GateDesc)) + align_up(nph * sizeof(double) + 8));
   if (!gates.empty()) std::memcpy(hg, gates.data(), gates.size() * sizeof(GateDesc));
   if (nph) std::memcpy(hph, final_phase, nph * sizeof(double));
-  CK(cudaMallocAsync((void**)&d_g, ng * sizeof(GateDesc), h->stream));
-  CK(cudaMallocAsync((void**)&d_disc, std::max(1, total) * sizeof(double), h->stream));
-  if (nph) CK(cudaMallocAsync((void**)&d_ph, nph * sizeof(double), h->stream));
+  CK(tmp_alloc(h, (void**)&d_g, ng * sizeof(GateDesc)));
+  CK(tmp_alloc(h, (void**)&d_disc, std::max(1, total) * sizeof(double)));
+  if (nph) CK(tmp_alloc(h, (void**)&d_ph, nph * sizeof(double)));
   if (!gates.empty())
     CK(cudaMemcpyAsync(d_g, hg, gates.size() * sizeof(GateDesc), cudaMemcpyHostToDevice, h->stream));
   if (nph) CK(cudaMemcpyAsync(d_ph, hph, nph * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   st = run_layers(h, d_g, loff, lcnt, d_disc, d_ph, nullptr);
   if (st == MPO_OK && discarded && total > 0)
     st = cuda_status(cudaMemcpyAsync(hdisc, d_disc, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  cudaFreeAsync(d_g, h->stream);
-  cudaFreeAsync(d_disc, h->stream);
-  if (d_ph) cudaFreeAsync(d_ph, h->stream);
+  tmp_free(h, d_g);
+  tmp_free(h, d_disc);
+  tmp_free(h, d_ph);
   if (st != MPO_OK) return st;
   st = poll_error(h);
   if (st == MPO_OK && discarded && total > 0) std::memcpy(discarded, hdisc, total * sizeof(double));
@@ -453,13 +497,13 @@ mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k, const d
   st = ensure_slots(h, maxl);
   if (st != MPO_OK) { delete pl; return st; }
   auto fail = [&](mpo_status s) { mpo_plan_destroy(pl); return s; };
-  if (cudaMalloc(&pl->d_gates, std::max<size_t>(1, gates.size()) * sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
-  if (cudaMalloc(&pl->d_disc, std::max(1, total) * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&pl->d_gates, std::max<size_t>(1, gates.size()) * sizeof(GateDesc)) != cudaSuccess) return fail(MPO_ERR_OOM);
+  if (dev_alloc(h, (void**)&pl->d_disc, std::max(1, total) * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
   if (!gates.empty() && cudaMemcpy(pl->d_gates, gates.data(), gates.size() * sizeof(GateDesc),
                                    cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(MPO_ERR_CUDA);
   if (final_phase) {
-    if (cudaMalloc(&pl->d_phase, (size_t)h->B * h->M * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
+    if (dev_alloc(h, (void**)&pl->d_phase, (size_t)h->B * h->M * sizeof(double)) != cudaSuccess) return fail(MPO_ERR_OOM);
     if (cudaMemcpy(pl->d_phase, final_phase, (size_t)h->B * h->M * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(MPO_ERR_CUDA);
   }
@@ -539,7 +583,7 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   std::vector<cudaEvent_t> ev((size_t)L * (NS + 1) + 2);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   unsigned long long* d_ctr = nullptr;
-  CK(cudaMallocAsync((void**)&d_ctr, CTR_N * sizeof(unsigned long long), h->stream));
+  CK(tmp_alloc(h, (void**)&d_ctr, CTR_N * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(d_ctr, 0, CTR_N * sizeof(unsigned long long), h->stream));
   MpoDev dv = h->dev;
   dv.ctr = d_ctr;
@@ -565,7 +609,7 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   unsigned long long ctr[CTR_N];
   CK(cudaMemcpyAsync(ctr, d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  cudaFreeAsync(d_ctr, h->stream);
+  tmp_free(h, d_ctr);
   // stage order: setup, theta, gram, order, svd, select, resplit, phases
   const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], 0.0,
                                   (double)(ctr[CTR_EIG] + ctr[CTR_REFINE]), 0.0, (double)ctr[CTR_RESPLIT], 0.0};
@@ -601,9 +645,9 @@ void mpo_plan_destroy(mpo_plan p) {
   }
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  if (p->d_gates) cudaFree(p->d_gates);
-  if (p->d_disc) cudaFree(p->d_disc);
-  if (p->d_phase) cudaFree(p->d_phase);
+  dev_free(p->h, p->d_gates);
+  dev_free(p->h, p->d_disc);
+  dev_free(p->h, p->d_phase);
   for (auto e : p->ev)
     if (e) cudaEventDestroy(e);
   delete p;
@@ -785,19 +829,28 @@ mpo_status mpo_sync(mpo_handle h) {
   return poll_error(h);
 }
 
+mpo_status mpo_set_allocator(mpo_alloc_fn alloc, mpo_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return MPO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_allocator_mu);
+  g_allocator.alloc = alloc;
+  g_allocator.free = free_fn;
+  g_allocator.ctx = alloc ? ctx : nullptr;
+  return MPO_OK;
+}
+
 void mpo_destroy(mpo_handle h) {
   if (!h) return;
   while (!h->plans.empty()) mpo_plan_destroy(h->plans.back());
   if (h->stream) cudaStreamSynchronize(h->stream);
-  if (h->state) cudaFree(h->state);
-  if (h->snap) cudaFree(h->snap);
-  if (h->d_err) cudaFree(h->d_err);
-  if (h->d_chicap) cudaFree(h->d_chicap);
-  if (h->ws_buf) cudaFree(h->ws_buf);
-  if (h->d_gate1) cudaFree(h->d_gate1);
-  if (h->d_disc1) cudaFree(h->d_disc1);
-  if (h->d_obs_scratch) cudaFree(h->d_obs_scratch);
-  if (h->d_obs_out) cudaFree(h->d_obs_out);
+  dev_free(h, h->state);
+  dev_free(h, h->snap);
+  dev_free(h, h->d_err);
+  dev_free(h, h->d_chicap);
+  dev_free(h, h->ws_buf);
+  dev_free(h, h->d_gate1);
+  dev_free(h, h->d_disc1);
+  dev_free(h, h->d_obs_scratch);
+  dev_free(h, h->d_obs_out);
   if (h->pin) cudaFreeHost(h->pin);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;

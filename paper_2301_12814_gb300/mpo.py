@@ -27,6 +27,7 @@ EXPORTS = [
     "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
     "mpo_asymptotic_ee", "mpo_asymptotic_ee_device", "mpo_checkpoint_bytes", "mpo_save", "mpo_load",
+    "mpo_set_allocator",
 ]
 ASYM_NMAX = 23  # MPO_ASYM_NMAX
 
@@ -74,6 +75,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_plan_stage_times": (_i, [_p, _dp]),
         "mpo_svd_cluster_shape": (_i, [_ip, _ip, _ip, _ip]),
         "mpo_checkpoint_bytes": (_i, [_p, ctypes.POINTER(ctypes.c_size_t)]),
+        "mpo_set_allocator": (_i, [_ALLOC_FN, _FREE_FN, _p]),
         "mpo_save": (_i, [_p, _p, ctypes.c_size_t, ctypes.c_longlong]),
         "mpo_load": (_i, [_p, _p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_longlong)]),
         "mpo_asymptotic_ee": (_i, [_i, _i, _dp, _dp, _dp, ctypes.c_double, _dp, _dp, _dp, _i]),
@@ -99,6 +101,33 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
 
 def _lib() -> ctypes.CDLL:
     return load_library()
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_ALLOCATOR_REFS = []  # keeps the installed ctypes callbacks alive
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Install a device allocator for handles created afterwards (mpo_set_allocator):
+    ``alloc(bytes, stream) -> int`` and ``free(ptr, stream)``, stream being the raw
+    cudaStream_t as an int; None, None restores the CUDA runtime."""
+    if alloc is None and free is None:
+        _check(_lib().mpo_set_allocator(_ALLOC_FN(), _FREE_FN(), None), "mpo_set_allocator")
+        return
+    a = _ALLOC_FN(lambda n, st, ctx: int(alloc(int(n), int(st or 0))) or None)
+    f = _FREE_FN(lambda ptr, st, ctx: free(int(ptr), int(st or 0)))
+    _ALLOCATOR_REFS.append((a, f))
+    _check(_lib().mpo_set_allocator(a, f, None), "mpo_set_allocator")
+
+
+def use_torch_allocator() -> None:
+    """Route handle memory through PyTorch's CUDA caching allocator on each handle's
+    stream (torch.cuda.caching_allocator_alloc / caching_allocator_delete)."""
+    import torch
+    dev = torch.cuda.current_device()
+    set_allocator(lambda n, st: torch.cuda.caching_allocator_alloc(n, device=dev, stream=st),
+                  lambda ptr, st: torch.cuda.caching_allocator_delete(ptr))
 
 
 def _d(a: Optional[np.ndarray]):

@@ -104,3 +104,13 @@ def test_checkpoint_argument_checks(lib):
     assert lib.mpo_checkpoint_bytes(None, ct.byref(n)) == 1
     assert lib.mpo_save(None, None, 0, 0) == 1
     assert lib.mpo_load(None, None, 0, None) == 1
+
+
+def test_allocator_argument_checks(lib):
+    from paper_2301_12814_gb300 import mpo
+    a = mpo._ALLOC_FN(lambda n, st, ctx: None)
+    f = mpo._FREE_FN(lambda p, st, ctx: None)
+    assert lib.mpo_set_allocator(a, mpo._FREE_FN(), None) == 1
+    assert lib.mpo_set_allocator(mpo._ALLOC_FN(), f, None) == 1
+    assert lib.mpo_set_allocator(a, f, None) == 0
+    assert lib.mpo_set_allocator(mpo._ALLOC_FN(), mpo._FREE_FN(), None) == 0
