@@ -107,9 +107,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(name: str, n_gates: int, repeats: int = 1) -> dict:
+def oracle_sample(name: str, n_gates: int, repeats: int = 1, threads: int = 1) -> dict:
+    """The oracle on the first n_gates gates, in a child process whose BLAS/OpenMP
+    thread count is pinned to `threads`."""
     env = dict(os.environ)
-    env.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", PYTHONPATH=ROOT)
+    t = str(int(threads))
+    env.update(OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, PYTHONPATH=ROOT)
     out = subprocess.run([sys.executable, "-m", "oracle.timing", name, str(n_gates), str(repeats)],
                          capture_output=True, text=True, env=env, cwd=ROOT, timeout=3600)
     if out.returncode != 0:
@@ -319,6 +322,11 @@ def run_native(args, ws, rank, local):
             res = oracle_sample(args.workload, n)
             cpu = {"value": res["updates_per_s"][0], "unit": "updates/s", "cores": res["cores"], "kind": "oracle",
                    "sample": f"first {n} gates of instance 0's mesh from the initial state ({res['seconds'][0]:.1f} s)"}
+            ncores = os.cpu_count() or 1
+            if ncores > 1:
+                res_all = oracle_sample(args.workload, n, threads=ncores)
+                cpu["all_cores"] = {"value": res_all["updates_per_s"][0], "cores": ncores,
+                                    "note": "same sample with BLAS/OpenMP threads = all host cores"}
         except Exception as e:  # the baseline is reported, never a reason to lose the GPU line
             cpu = {"value": None, "unit": "updates/s", "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {str(e)[-200:]}"}

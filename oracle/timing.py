@@ -16,6 +16,12 @@ import sys
 import time
 
 
+def _cores(threads: dict) -> int:
+    """Threads the BLAS/OpenMP environment allows (all host cores when unset)."""
+    vals = [int(v) for v in threads.values() if v and v.isdigit()]
+    return min(vals) if vals else (os.cpu_count() or 1)
+
+
 def run(name: str, n_gates: int, repeats: int = 1) -> dict:
     import gbs_workloads as w
     from . import u1mpo
@@ -37,7 +43,7 @@ def run(name: str, n_gates: int, repeats: int = 1) -> dict:
         "workload": name, "gates": n, "seconds": times, "init_seconds": t1 - t0,
         "updates_per_s": [n / t for t in times], "trace": tr, "n_mean": list(n1), "n2_mean": list(n2),
         "entropy": list(P.entropy), "discarded_sum": float(sum(P.discarded)),
-        "cores": 1 if all(v == "1" for v in threads.values()) else os.cpu_count(), "threads_env": threads,
+        "cores": _cores(threads), "threads_env": threads,
     }
 
 
@@ -55,8 +61,7 @@ def run_asymptotic(n_points: int, repeats: int = 1) -> dict:
         times.append(time.perf_counter() - t0)
     threads = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     return {"workload": g.name, "points": n, "seconds": times, "points_per_s": [n / t for t in times],
-            "S": S, "cores": 1 if all(v == "1" for v in threads.values()) else os.cpu_count(),
-            "threads_env": threads}
+            "S": S, "cores": _cores(threads), "threads_env": threads}
 
 
 if __name__ == "__main__":
