@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -180,12 +181,25 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   const long long D = h->D;
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
-  w.capTheta = (long long)h->Pc * D * D;
-  // per-slot budget for each of the Theta-sized complex arrays (Theta, W, G, V, NS, VC): 512 MiB
-  const long long budget = (2ll << 30) / (4 * (long long)sizeof(double2));
-  if (w.capTheta > budget) w.capTheta = budget;
+  w.capTheta = (long long)h->Pc * D * D;  // one slot's worst case
   w.capGram = w.capTheta;
   const int S = need;
+  // Theta, W, G, V, NS and VC are pools shared by a layer's slots (k_setup lays them
+  // out from the actual block sizes, which are far below the worst case S x Pc D^2 at
+  // large chi).  Each pool holds the worst case if that fits a budget for the six
+  // pools -- GBS_MPO_WORKSPACE_GB, else a quarter of the free device memory -- and the
+  // budget otherwise; a layer whose blocks do not fit fails with MPO_ERR_CAPACITY.
+  {
+    const long long worst = (long long)S * w.capTheta;
+    size_t freeb = 0, totalb = 0;
+    CK(cudaMemGetInfo(&freeb, &totalb));
+    const char* env = getenv("GBS_MPO_WORKSPACE_GB");
+    const double gb = env ? atof(env) : 0.0;
+    const double bytes = gb > 0.0 ? gb * (double)(1ll << 30) : 0.25 * (double)freeb;
+    const long long budget = std::max(1ll, (long long)(bytes / (6.0 * sizeof(double2))));
+    w.poolTheta = std::min(worst, budget);
+    w.poolGram = w.poolTheta;
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   size_t o_blk = take((size_t)S * BF_NFIELDS * (w.Pc + 1) * sizeof(int));
@@ -195,19 +209,21 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_rm = take((size_t)S * w.capRC * sizeof(int));
   size_t o_cm = take((size_t)S * w.capRC * sizeof(int));
   size_t o_fk = take((size_t)S * MPO_FOCK_MAX * sizeof(double2));
-  size_t o_th = take((size_t)S * w.capTheta * sizeof(double2));
-  size_t o_g = take((size_t)S * w.capGram * sizeof(double2));
-  size_t o_v = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_th = take((size_t)w.poolTheta * sizeof(double2));
+  size_t o_g = take((size_t)w.poolGram * sizeof(double2));
+  size_t o_v = take((size_t)w.poolGram * sizeof(double2));
   size_t o_sv = take((size_t)S * w.capCand * sizeof(double));
   size_t o_pm = take((size_t)S * w.capCand * sizeof(int));
   size_t o_ds = take((size_t)S * 4 * sizeof(double));
   size_t o_or = take((size_t)S * w.capCand * 2 * sizeof(int));
   size_t o_it = take((size_t)S * w.P * w.P * sizeof(int));
-  size_t o_w = take((size_t)S * w.capTheta * sizeof(double2));
-  size_t o_ns = take((size_t)S * w.capGram * sizeof(double2));
-  size_t o_vc = take((size_t)S * w.capGram * sizeof(double2));
+  size_t o_w = take((size_t)w.poolTheta * sizeof(double2));
+  size_t o_ns = take((size_t)w.poolGram * sizeof(double2));
+  size_t o_vc = take((size_t)w.poolGram * sizeof(double2));
   size_t o_ls = take((size_t)S * w.Pc * sizeof(int));
   size_t o_ct = take(8 * sizeof(int));
+  size_t o_po = take((size_t)S * 2 * sizeof(long long));
+  size_t o_sc = take(sizeof(unsigned int));
   void* buf = nullptr;
   CK(dev_alloc(h, &buf, off));
   CK(cudaMemsetAsync(buf, 0, off, h->stream));
@@ -218,6 +234,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   w.V = (double2*)(b + o_v); w.sval = (double*)(b + o_sv); w.perm = (int*)(b + o_pm);
   w.dscal = (double*)(b + o_ds); w.order = (int*)(b + o_or); w.items = (int*)(b + o_it); w.W = (double2*)(b + o_w); w.NS = (double2*)(b + o_ns); w.VC = (double2*)(b + o_vc);
   w.list = (int*)(b + o_ls); w.counter = (int*)(b + o_ct);
+  w.poff = (long long*)(b + o_po); w.sctr = (unsigned int*)(b + o_sc);
   h->ws_buf = buf;
   h->ws = w;
   h->nslots = S;

@@ -146,17 +146,18 @@ __device__ __forceinline__ Slot get_slot(const SlotWS& ws, int s) {
   sl.rowmap = ws.rowmap + (long long)s * ws.capRC;
   sl.colmap = ws.colmap + (long long)s * ws.capRC;
   sl.fock = ws.fock + (long long)s * MPO_FOCK_MAX;
-  sl.theta = ws.theta + (long long)s * ws.capTheta;
-  sl.G = ws.G + (long long)s * ws.capGram;
-  sl.V = ws.V + (long long)s * ws.capGram;
+  const long long pt = ws.poff[2 * s], pg = ws.poff[2 * s + 1];
+  sl.theta = ws.theta + pt;
+  sl.G = ws.G + pg;
+  sl.V = ws.V + pg;
   sl.sval = ws.sval + (long long)s * ws.capCand;
   sl.perm = ws.perm + (long long)s * ws.capCand;
   sl.dscal = ws.dscal + (long long)s * 4;
   sl.order = ws.order + (long long)s * ws.capCand * 2;
   sl.items = ws.items + (long long)s * ws.P * ws.P;
-  sl.W = ws.W + (long long)s * ws.capTheta;
-  sl.NS = ws.NS + (long long)s * ws.capGram;
-  sl.VC = ws.VC + (long long)s * ws.capGram;
+  sl.W = ws.W + pt;
+  sl.NS = ws.NS + pg;
+  sl.VC = ws.VC + pg;
   return sl;
 }
 
@@ -177,7 +178,7 @@ __device__ __forceinline__ int box_count(const int* S, int q, int x0, int x1, in
 }
 
 // ---------------------------------------------------------------- k_setup
-__global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+__device__ void setup_gate(const MpoDev& st, const SlotWS& ws, const GateDesc* __restrict__ gates) {
   const int s = blockIdx.x;
   const GateDesc g = gates[s];
   Slot sl = get_slot(ws, s);
@@ -322,9 +323,11 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
       gt += ntg * (ntg + 1) / 2;
     }
     sl.f(BF_GT, Pc) = gt;
-    sl.f(BF_TOFF, Pc) = (int)toff; sl.f(BF_COFF, Pc) = (int)coff;
+    sl.f(BF_TOFF, Pc) = (int)toff; sl.f(BF_COFF, Pc) = (int)coff; sl.f(BF_GOFF, Pc) = (int)goff;
     int status = 0;
-    if (toff > ws.capTheta || goff > ws.capGram || coff > ws.capCand || rm > ws.capRC || cm2 > ws.capRC) {
+    // Theta and Gram sizes go to the layer's pools (checked once all slots are known);
+    // here only what one slot's fixed-size arrays and 32-bit offsets can hold
+    if (toff > 0x7fffffffll || goff > 0x7fffffffll || coff > ws.capCand || rm > ws.capRC || cm2 > ws.capRC) {
       status = 1;
       dev_set_error(st.err, DEV_ERR_CAPACITY, 2000);
     }
@@ -386,6 +389,80 @@ __global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateD
       }
     }
   }
+}
+
+// The last CTA of k_setup to finish lays out the layer's pools: slot s's Theta-sized
+// and Gram-sized regions start at the exclusive prefix sums of the slots' sizes (zero for
+// a slot whose setup failed).  If the layer does not fit the pools, every slot of the
+// layer is marked failed (MPO_ERR_CAPACITY), so no later kernel touches the pools.
+// Then the arrival counter is reset for the next layer.
+__device__ void pool_offsets(const MpoDev& st, const SlotWS& ws) {
+  __shared__ int last;
+  __shared__ long long part[2][256 / 32];
+  __syncthreads();
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(ws.sctr, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // each thread sums a contiguous chunk of slots, then a block-wide exclusive scan
+  const int S = gridDim.x, Pc = ws.Pc;
+  const int chunk = (S + nth - 1) / nth, s0 = min(S, tid * chunk), s1 = min(S, s0 + chunk);
+  long long nt = 0, ng = 0;
+  for (int s = s0; s < s1; ++s) {
+    volatile const int* scal = ws.scal + (long long)s * SS_NFIELDS;
+    volatile const int* blk = ws.blk + (long long)s * BF_NFIELDS * (Pc + 1);
+    if (scal[SS_STATUS] == 0) {
+      nt += blk[BF_TOFF * (Pc + 1) + Pc];
+      ng += blk[BF_GOFF * (Pc + 1) + Pc];
+    }
+  }
+  long long it = nt, ig = ng;  // inclusive warp scans
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long ut = __shfl_up_sync(0xffffffffu, it, o), ug = __shfl_up_sync(0xffffffffu, ig, o);
+    if (lane >= o) { it += ut; ig += ug; }
+  }
+  if (lane == 31) { part[0][warp] = it; part[1][warp] = ig; }
+  __syncthreads();
+  long long bt = 0, bg = 0, tt = 0, tg = 0;
+  for (int w = 0; w < nth / 32; ++w) {
+    if (w < warp) { bt += part[0][w]; bg += part[1][w]; }
+    tt += part[0][w]; tg += part[1][w];
+  }
+  long long t = bt + it - nt, g = bg + ig - ng;  // exclusive prefix of this chunk
+  for (int s = s0; s < s1; ++s) {
+    volatile const int* scal = ws.scal + (long long)s * SS_NFIELDS;
+    volatile const int* blk = ws.blk + (long long)s * BF_NFIELDS * (Pc + 1);
+    ws.poff[2 * s] = t;
+    ws.poff[2 * s + 1] = g;
+    if (scal[SS_STATUS] == 0) {
+      t += blk[BF_TOFF * (Pc + 1) + Pc];
+      g += blk[BF_GOFF * (Pc + 1) + Pc];
+    }
+  }
+  __syncthreads();  // every slot's status has been read before any is overwritten
+  if (tt > ws.poolTheta || tg > ws.poolGram) {
+    if (tid == 0) dev_set_error(st.err, DEV_ERR_CAPACITY, 2001);
+    for (int s = tid; s < S; s += nth) {
+      int* scal = ws.scal + (long long)s * SS_NFIELDS;
+      scal[SS_STATUS] = 1;
+      scal[SS_GTILES] = 0;
+      scal[SS_TTILES] = 0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    *ws.sctr = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_setup(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+  setup_gate(st, ws, gates);
+  pool_offsets(st, ws);
 }
 
 // ---------------------------------------------------------------- k_theta

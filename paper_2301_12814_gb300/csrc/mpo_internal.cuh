@@ -120,6 +120,13 @@ struct SlotWS {
                    // (never aliases the FP32 Gram or seed buffers of other blocks)
   int* list;       // [S * Pc] layer's blocks, longest first (k_order)
   int* counter;    // [8]: cursors and ends of the cluster, CTA and warp parts of list (k_order)
+  // Theta, W (poolTheta entries each) and G, V, NS, VC (poolGram entries each) are pools
+  // shared by the slots of a layer: slot s's region starts at poff[2s] (Theta-sized)
+  // and poff[2s + 1] (Gram-sized), laid out by the last CTA of k_setup from the slots'
+  // actual sizes.  capTheta / capGram are one slot's worst case.
+  long long poolTheta, poolGram;
+  long long* poff;       // [S][2]
+  unsigned int* sctr;    // k_setup arrival counter (the last CTA lays out the pools, resets it)
 };
 
 __host__ __device__ inline int pair_c(int p, int ncap) { return p / (ncap + 1); }
