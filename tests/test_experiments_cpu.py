@@ -19,3 +19,55 @@ def test_plateau_stop_rule():
     # patience 10 as in App. A
     seq = [0.1 * i for i in range(12)] + [1.0] * 10
     assert stop(seq, patience=10) == 21
+
+
+def _fake_protocol(monkeypatch, err_of_chi):
+    """Run experiments.fig4b / bond_dimension_search with the GPU calls replaced by a
+    known error curve, recording every chi the protocol asks for."""
+    import paper_2301_12814_gb300.experiments as ex
+    asked = []
+
+    def fake_curve(M, d, r, eta, k, theta, phi, final_phase=None, chis=(), precision="fp64", n_cap=None):
+        asked.append(list(chis))
+        return [(int(c), float(err_of_chi(M, int(c)))) for c in chis]
+
+    monkeypatch.setattr(ex, "truncation_curve", fake_curve)
+    monkeypatch.setattr(ex, "choose_d", lambda M, r, eta, **kw: {"d": 9, "n_cap": 8, "d_in": 32, "tail": 0.005,
+                                                                   "visited": [(9, 0.005)]})
+    monkeypatch.setattr(ex, "_truncation_error",
+                        lambda M, d, r, eta, chi, *a, **kw: float(err_of_chi(M, int(chi))))
+    return ex, asked
+
+
+def test_fig4b_bracket_and_refinement(monkeypatch):
+    """Doubling phase in one batch, then evenly spaced chi inside the first bracket
+    that meets the target; the answer is the smallest refined chi within target."""
+    err = lambda M, chi: 8.0 / chi  # 0.02 is first met at chi = 400: bracket (256, 512]
+    ex, asked = _fake_protocol(monkeypatch, err)
+    res = ex.fig4b(chi_max=1024, target=0.02, refine=3)
+    assert len(res) == 3
+    r0 = res[0]
+    assert [c for c, _ in r0["curve"]] == [8, 16, 32, 64, 128, 256, 512, 1024]
+    assert [c for c, _ in r0["refined"]] == [320, 384, 448]
+    assert r0["chi_for_target"] == 448 and abs(r0["error_at_chi"] - 8.0 / 448) < 1e-15
+    # two batched calls per configuration
+    assert len(asked) == 6 and asked[1] == [320, 384, 448]
+
+
+def test_fig4b_target_not_reached(monkeypatch):
+    ex, asked = _fake_protocol(monkeypatch, lambda M, chi: 0.5)
+    res = ex.fig4b(chi_max=64)
+    assert all(r["chi_for_target"] is None and r["refined"] == [] for r in res)
+    assert len(asked) == 3  # no refinement batch
+
+
+def test_bond_dimension_search_doubling_then_bisection(monkeypatch):
+    """App. A: double from chi0 while the error exceeds the target, then bisect the
+    last bracket; every visited chi below the answer failed the target."""
+    ex, _ = _fake_protocol(monkeypatch, lambda M, chi: 10.0 / chi)  # target 0.02 met from chi = 500
+    res = ex.bond_dimension_search(8, 9, [0.88] * 8, [0.3] * 8, [0], [0.1], [0.2], chi0=8, target=0.02, refine=4)
+    chis = [c for c, _ in res["visited"]]
+    assert chis[:7] == [8, 16, 32, 64, 128, 256, 512]
+    assert res["chi"] >= 500 and 10.0 / res["chi"] <= 0.02
+    assert all(e > 0.02 for c, e in res["visited"] if c < res["chi"])
+    assert len(chis) == 7 + 4
