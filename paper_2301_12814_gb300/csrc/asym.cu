@@ -243,9 +243,18 @@ __device__ void asym_item(int sec, int pt, int n, const double* __restrict__ r_a
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (act && fabs(ga) > gfloor && fabs(ga) > ASYM_TOL * sqrt(al * be)) {
+        if (act && fabs(ga) > gfloor && ga * ga > ASYM_TOL * ASYM_TOL * (al * be)) {
+          // the tangent t of the rotation angle in FP32 (from the FP64 ratio zeta); c and
+          // s = c t in FP64 keep the rotation orthogonal to FP64 rounding whatever t is,
+          // so only the angle, not the accuracy of the singular values, is FP32
           const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+          double t;
+          if (fabs(zeta) < 1e18) {
+            const float zf = (float)zeta;
+            t = (double)(copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f))));
+          } else {
+            t = 0.5 / zeta;
+          }
           const double c = rsqrt(fma(t, t, 1.0)), s = c * t;
           for (int e = sub; e < nb; e += g) {
             const double x = ap[e], y = aq[e];
