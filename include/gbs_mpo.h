@@ -46,7 +46,10 @@ typedef enum {
   MPO_ERR_CUDA = 3,      /* a CUDA runtime call failed                           */
   MPO_ERR_NUMERIC = 4,   /* eigensolver sweep cap reached or a non-finite value  */
   MPO_ERR_TIMEOUT = 5,   /* reserved: a bounded device wait ran out              */
-  MPO_ERR_CAPACITY = 6,  /* a per-gate workspace bound was exceeded on device    */
+  MPO_ERR_CAPACITY = 6,  /* a workspace bound was exceeded on device: the layer's
+                            pools of Theta- and Gram-sized arrays (sized at most to
+                            GBS_MPO_WORKSPACE_GB, else a quarter of the free device
+                            memory) or a per-gate table                            */
   MPO_ERR_INTERNAL = 7,  /* a device-side consistency check failed               */
   MPO_ERR_POISONED = 8,  /* handle unusable after an earlier device-side error   */
   MPO_ERR_NOT_BUILT = 9  /* the CUDA library could not be loaded or has no GPU   */

@@ -308,7 +308,7 @@ const char* mpo_status_string(mpo_status s) {
     case MPO_ERR_CUDA: return "CUDA runtime error";
     case MPO_ERR_NUMERIC: return "numerical failure (eigensolver sweep cap or non-finite value)";
     case MPO_ERR_TIMEOUT: return "bounded device wait ran out";
-    case MPO_ERR_CAPACITY: return "per-gate workspace capacity exceeded";
+    case MPO_ERR_CAPACITY: return "workspace capacity exceeded (layer pools or a per-gate table)";
     case MPO_ERR_INTERNAL: return "device consistency check failed";
     case MPO_ERR_POISONED: return "handle poisoned by an earlier device error";
     case MPO_ERR_NOT_BUILT: return "CUDA library unavailable";
