@@ -22,8 +22,7 @@ can carry non-zero U(1)-symmetric MPO entanglement).
 """
 from __future__ import annotations
 
-import math
-from typing import Dict, List, Sequence
+from typing import List, Sequence
 
 import numpy as np
 

@@ -40,7 +40,7 @@ Readings of points the paper leaves open (each is listed in the design notes):
 from __future__ import annotations
 
 import math
-from typing import List, Optional, Sequence, Tuple
+from typing import List, Optional, Sequence
 
 import numpy as np
 

@@ -2,7 +2,6 @@
 include/gbs_mpo.h and libgbsmpo.so): it compiles and links on any machine; on a GPU
 it runs a truncated mesh, a checkpoint round trip and one App. C estimate, and prints
 the same numbers the Python binding computes."""
-import math
 import os
 import shutil
 import subprocess

@@ -2,8 +2,6 @@
 citation)."""
 import os
 
-import numpy as np
-
 from oracle import u1mpo
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")

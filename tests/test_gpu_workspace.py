@@ -3,7 +3,6 @@ gates, laid out by k_setup from the actual block sizes): a budget too small for 
 layer fails that call with MPO_ERR_CAPACITY and poisons the handle, with no device
 fault; a handle built afterwards with the normal budget runs the same mesh to the
 oracle's numbers."""
-import os
 
 import numpy as np
 import pytest
