@@ -114,6 +114,17 @@ void tmp_free(const mpo_ctx* h, void* p) {
   else cudaFreeAsync(p, h->stream);
 }
 
+// Runs a cleanup when the scope ends, on error returns too.
+template <typename F>
+struct ScopeExit {
+  F f;
+  ~ScopeExit() { f(); }
+};
+template <typename F>
+ScopeExit<F> on_scope_exit(F f) {
+  return ScopeExit<F>{f};
+}
+
 mpo_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MPO_OK;
   if (e == cudaErrorMemoryAllocation) return MPO_ERR_OOM;
@@ -173,7 +184,12 @@ mpo_status poll_error(mpo_handle h) {
 
 mpo_status ensure_slots(mpo_handle h, int need) {
   if (need <= h->nslots) return MPO_OK;
-  if (h->ws_buf) { CK(cudaStreamSynchronize(h->stream)); dev_free(h, h->ws_buf); h->ws_buf = nullptr; }
+  if (h->ws_buf) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->ws_buf);
+    h->ws_buf = nullptr;
+    h->nslots = 0;  // no workspace until the new one is in place
+  }
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
   w.big_min = svd_big_min();
@@ -226,7 +242,11 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   size_t o_sc = take(sizeof(unsigned int));
   void* buf = nullptr;
   CK(dev_alloc(h, &buf, off));
-  CK(cudaMemsetAsync(buf, 0, off, h->stream));
+  const cudaError_t me = cudaMemsetAsync(buf, 0, off, h->stream);
+  if (me != cudaSuccess) {
+    dev_free(h, buf);
+    return cuda_status(me);
+  }
   char* b = (char*)buf;
   w.blk = (int*)(b + o_blk); w.scal = (int*)(b + o_scal); w.rowoff = (int*)(b + o_ro);
   w.coloff = (int*)(b + o_co); w.rowmap = (int*)(b + o_rm); w.colmap = (int*)(b + o_cm);
@@ -460,6 +480,11 @@ mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k, const 
   st = ensure_slots(h, maxl);
   if (st != MPO_OK) return st;
   GateDesc* d_g = nullptr; double* d_disc = nullptr; double* d_ph = nullptr;
+  auto release = on_scope_exit([&] {
+    tmp_free(h, d_g);
+    tmp_free(h, d_disc);
+    tmp_free(h, d_ph);
+  });
   const size_t ng = std::max<size_t>(1, gates.size());
   const size_t nph = final_phase ? (size_t)h->B * h->M : 0;
   // pinned staging: [gates | phases | discarded]
@@ -487,9 +512,6 @@ mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k, const 
   st = run_layers(h, d_g, loff, lcnt, d_disc, d_ph, nullptr);
   if (st == MPO_OK && discarded && total > 0)
     st = cuda_status(cudaMemcpyAsync(hdisc, d_disc, total * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  tmp_free(h, d_g);
-  tmp_free(h, d_disc);
-  tmp_free(h, d_ph);
   if (st != MPO_OK) return st;
   st = poll_error(h);
   if (st == MPO_OK && discarded && total > 0) std::memcpy(discarded, hdisc, total * sizeof(double));
@@ -597,9 +619,14 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   if (h->poisoned) return MPO_ERR_POISONED;
   const int L = (int)p->layer_off.size();
   constexpr int NS = MPO_NSTAGES - 1;  // per-layer stages; the last stage is the phase screen
-  std::vector<cudaEvent_t> ev((size_t)L * (NS + 1) + 2);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
+  std::vector<cudaEvent_t> ev((size_t)L * (NS + 1) + 2, nullptr);
   unsigned long long* d_ctr = nullptr;
+  auto release = on_scope_exit([&] {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    tmp_free(h, d_ctr);
+  });
+  for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(tmp_alloc(h, (void**)&d_ctr, CTR_N * sizeof(unsigned long long)));
   CK(cudaMemsetAsync(d_ctr, 0, CTR_N * sizeof(unsigned long long), h->stream));
   MpoDev dv = h->dev;
@@ -622,11 +649,9 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
   float tp = 0.f;
   CK(cudaEventElapsedTime(&tp, ev[(size_t)L * (NS + 1)], ev[(size_t)L * (NS + 1) + 1]));
   ms[NS] = tp;
-  for (auto& e : ev) cudaEventDestroy(e);
   unsigned long long ctr[CTR_N];
   CK(cudaMemcpyAsync(ctr, d_ctr, sizeof(ctr), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  tmp_free(h, d_ctr);
   // stage order: setup, theta, gram, order, svd, select, resplit, phases
   const double fl[MPO_NSTAGES] = {0.0, (double)ctr[CTR_THETA], (double)ctr[CTR_GRAM], 0.0,
                                   (double)(ctr[CTR_EIG] + ctr[CTR_REFINE]), 0.0, (double)ctr[CTR_RESPLIT], 0.0};
