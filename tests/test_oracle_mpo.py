@@ -155,6 +155,40 @@ def test_mesh_exact_matches_dense(M, d, seed):
         assert abs(np.diag(D.rho).real[sel].sum() - np.diag(D0.rho).real[sel].sum()) < 1e-13
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_random_exact_configurations_match_dense(seed):
+    """Seeded random exact cases: 2-4 modes, cutoffs up to 5 (d^M <= 256), a random cap
+    n_cap <= d - 1, per-mode r and eta (vacuum and lossless modes included), random
+    nearest-neighbour gates.  O2 must equal O1 entry by entry, and in its moments and
+    U(1)-form entanglement at every cut."""
+    rng = np.random.default_rng(300 + seed)
+    M = int(rng.integers(2, 5))
+    d = int(rng.integers(2, 6))
+    while d ** M > 256:
+        d -= 1
+    n_cap = int(rng.integers(1, d)) if rng.uniform() < 0.5 else None
+    r = rng.uniform(0.0, 1.3, M)
+    r[rng.uniform(size=M) < 0.2] = 0.0
+    eta = rng.uniform(0.0, 1.0, M)
+    eta[rng.uniform(size=M) < 0.2] = 1.0
+    ng = int(rng.integers(1, 3 * M))
+    k = rng.integers(0, M - 1, ng)
+    th = rng.uniform(0, np.pi / 2, ng)
+    ph = rng.uniform(0, 2 * np.pi, ng)
+    D = dense.DenseState(M, d, r, eta, n_cap=n_cap)
+    P = u1mpo.U1MPO(M, d, r, eta, n_cap=n_cap)
+    for kk, t, p in zip(k, th, ph):
+        D.apply_gate(int(kk), w.gate_block(float(t), float(p)))
+    P.run_mesh(k, th, ph)
+    assert np.abs(P.to_dense() - D.rho).max() < 1e-13
+    trD, n1D, n2D = D.moments()
+    trP, n1P, n2P = P.observables()
+    assert abs(trP - trD) < 1e-13
+    assert np.abs(n1P - n1D).max() < 1e-13 and np.abs(n2P - n2D).max() < 1e-13
+    for b in range(M + 1):
+        assert abs(P.entropy[b] - D.u1_entropy(b)) < 1e-11
+
+
 def test_first_moments_exact_larger_mesh():
     """M = 8 with the cap active and no truncation: O2's <n> equals |U|^2 <n_in>_cap;
     this also fixes the U versus U^T convention of the gate list."""
