@@ -338,6 +338,7 @@ const char* mpo_status_string(mpo_status s) {
 
 mpo_status mpo_init_lossy_squeezed(mpo_handle* out, const mpo_params* p, const double* r,
                                    const double* eta) {
+  NvtxRange nv("gbs_mpo/init");
   if (!out || !p || !r || !eta) return MPO_ERR_ARG;
   *out = nullptr;
   const int M = p->M, d = p->d, B = p->batch;
@@ -449,6 +450,7 @@ mpo_status mpo_reset(mpo_handle h) {
 }
 
 mpo_status mpo_apply_bs(mpo_handle h, int inst, int k, double theta, double phi, double* discarded_weight) {
+  NvtxRange nv("gbs_mpo/apply_bs");
   if (!h) return MPO_ERR_ARG;
   if (h->poisoned) return MPO_ERR_POISONED;
   if (inst < 0 || inst >= h->B || k < 0 || k > h->M - 2 || !std::isfinite(theta) || !std::isfinite(phi))
@@ -468,6 +470,7 @@ mpo_status mpo_apply_bs(mpo_handle h, int inst, int k, double theta, double phi,
 
 mpo_status mpo_sweep_mesh(mpo_handle h, const int* n_gates, const int* k, const double* theta,
                           const double* phi, const double* final_phase, double* discarded) {
+  NvtxRange nv("gbs_mpo/sweep_mesh");
   if (!h || !n_gates || !k || !theta || !phi) return MPO_ERR_ARG;
   if (h->poisoned) return MPO_ERR_POISONED;
   std::vector<GateDesc> gates;
@@ -567,6 +570,7 @@ mpo_status mpo_plan_mesh(mpo_handle h, const int* n_gates, const int* k, const d
 }
 
 mpo_status mpo_plan_run(mpo_plan p) {
+  NvtxRange nv("gbs_mpo/plan_run");
   if (!p || !p->h) return MPO_ERR_ARG;
   if (p->h->poisoned) return MPO_ERR_POISONED;
   CK(cudaGraphLaunch(p->exec, p->h->stream));

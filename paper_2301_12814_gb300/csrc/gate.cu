@@ -2720,25 +2720,35 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (per < 1) per = 1;
   if (per > 4096) per = 4096;
   const int nblk = ngates * ws.Pc;
+  NvtxRange layer("gbs_mpo/layer");
   if (ev) record_stage_event(ev[0], st);
-  k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates);
+  { NvtxRange r("gbs_mpo/k_setup"); k_setup<<<ngates, 256, 0, st>>>(s, ws, d_gates); }
   if (ev) record_stage_event(ev[1], st);
-  k_theta<R><<<dim3(per, ngates), THETA_WARPS * 32, theta_smem_bytes(s.ncap, sizeof(typename Prec<R>::C)), st>>>(
-      s, ws, d_gates);
+  {
+    NvtxRange r("gbs_mpo/k_theta");
+    k_theta<R><<<dim3(per, ngates), THETA_WARPS * 32, theta_smem_bytes(s.ncap, sizeof(typename Prec<R>::C)), st>>>(
+        s, ws, d_gates);
+  }
   if (ev) record_stage_event(ev[2], st);
-  k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr);
+  { NvtxRange r("gbs_mpo/k_gram"); k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr); }
   if (ev) record_stage_event(ev[3], st);
   const int svd_ctas = svd_grid<R>(nblk);
   const SvdLayout SL = svd_layout<R>(ws.D, SVD_SMEM);
   const int seed_max = (int)sqrt((double)(SL.total - SL.data) / (2.0 * sizeof(float2)));
   const int room = sizeof(R) == 4 ? (int)(SL.total - SL.data) : 0;
-  k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max, room);
+  {
+    NvtxRange r("gbs_mpo/k_order");
+    k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max, room);
+  }
   if (ev) record_stage_event(ev[4], st);
-  launch_svd<R>(s, ws, d_gates, svd_ctas, st);
+  { NvtxRange r("gbs_mpo/k_svd"); launch_svd<R>(s, ws, d_gates, svd_ctas, st); }
   if (ev) record_stage_event(ev[5], st);
-  k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor);
+  { NvtxRange r("gbs_mpo/k_select"); k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor); }
   if (ev) record_stage_event(ev[6], st);
-  k_resplit<R><<<dim3(per, ngates), 256, 2 * (size_t)s.D * sizeof(double), st>>>(s, ws, d_gates);
+  {
+    NvtxRange r("gbs_mpo/k_resplit");
+    k_resplit<R><<<dim3(per, ngates), 256, 2 * (size_t)s.D * sizeof(double), st>>>(s, ws, d_gates);
+  }
   if (ev) record_stage_event(ev[7], st);
 }
 

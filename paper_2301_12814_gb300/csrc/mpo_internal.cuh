@@ -16,7 +16,17 @@
 // once, one slot each).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
+
+// Host-side NVTX range for the enclosing scope (named gbs_mpo/<what>): marks each
+// stage launch and each entry point for Nsight tools; free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define MPO_NCAP_MAX 15
 #define MPO_P_MAX ((MPO_NCAP_MAX + 1) * (MPO_NCAP_MAX + 1))
