@@ -3,6 +3,16 @@
 Names follow the C ABI of include/gbs_mpo.h.  The library is loaded from this
 package directory; if it is missing or cannot be loaded the binding raises
 instead of falling back to anything else.
+
+* ``MPO``: a handle (mpo_init_lossy_squeezed) with gates (apply_bs, sweep_mesh,
+  plan_mesh), observables, entropies, bonds, the truncated probability, checkpoints
+  (save / load) and reset.
+* ``Plan``: a mesh captured in a CUDA graph, with per-stage times and an instrumented
+  profile.
+* ``asymptotic_ee`` / ``asymptotic_ee_device``: the App. C estimator.
+* ``set_allocator`` / ``use_torch_allocator``: device memory of later handles from a
+  caller's allocator (mpo_set_allocator).
+* ``svd_cluster_shape``: the block SVD's launch shape on this GPU.
 """
 from __future__ import annotations
 
