@@ -193,7 +193,15 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
   w.big_min = svd_big_min();
-  w.cl_seed_max = svd_cluster_seed_max();
+  // Cluster blocks on the FP64 path all run the FP32 one-sided cluster phase: its seed
+  // keeps the small singular values (a Gram seed squares their conditioning), so the
+  // critical blocks' FP64 polish needs 2 sweeps instead of 3 to 4 (16 modes, chi = 64:
+  // 6543 -> 8218 updates/s).  On the FP32 path the single-CTA Gram seed stays for Gram
+  // sides up to 64.  GBS_MPO_SVD_CLUSTER_SEED_MAX overrides both.
+  {
+    const int sm = svd_cluster_seed_max();
+    w.cl_seed_max = sm >= 0 ? sm : (h->prec == MPO_FP64 ? 0 : 64);
+  }
   const long long D = h->D;
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;

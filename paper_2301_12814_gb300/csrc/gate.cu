@@ -2790,13 +2790,13 @@ int svd_big_min() {
   return v;
 }
 
-// Largest Gram side of a cluster block that takes the single-CTA Gram seed: 64, or
-// GBS_MPO_SVD_CLUSTER_SEED_MAX (>= 0) from the environment (0 makes every cluster
-// block run the FP32 cluster phase; the tests use it).
+// Largest Gram side of a cluster block that takes the single-CTA Gram seed, from
+// GBS_MPO_SVD_CLUSTER_SEED_MAX (>= 0) in the environment; -1 when it is not set (the
+// handle then chooses by precision: 0 on the FP64 path, 64 on the FP32 path).
 int svd_cluster_seed_max() {
-  static int v = -1;
-  if (v < 0) {
-    v = 64;
+  static int v = -2;
+  if (v == -2) {
+    v = -1;
     const char* e = getenv("GBS_MPO_SVD_CLUSTER_SEED_MAX");
     if (e && atoi(e) >= 0) v = atoi(e);
   }

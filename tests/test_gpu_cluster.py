@@ -21,14 +21,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 @pytest.fixture(scope="module", params=["gram_seed", "fp32_phase"])
 def results(request):
     """Every block on a cluster; cluster blocks of Gram side <= 64 seeded by the
-    single-CTA Gram eigensolver (the default), or all of them by the FP32 cluster
-    phase (GBS_MPO_SVD_CLUSTER_SEED_MAX=0)."""
+    single-CTA Gram eigensolver (GBS_MPO_SVD_CLUSTER_SEED_MAX=64, the FP32 path's
+    default), or all of them by the FP32 cluster phase (=0, the FP64 path's default)."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     env = dict(os.environ, GBS_MPO_SVD_CLUSTER_MIN_N="1")
-    if request.param == "fp32_phase":
-        env["GBS_MPO_SVD_CLUSTER_SEED_MAX"] = "0"
+    env["GBS_MPO_SVD_CLUSTER_SEED_MAX"] = "0" if request.param == "fp32_phase" else "64"
     out = subprocess.run([sys.executable, os.path.join(HERE, "cluster_route_check.py")], env=env,
                          capture_output=True, text=True, timeout=1200)
     assert out.returncode == 0, out.stderr[-3000:]
