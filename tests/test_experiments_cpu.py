@@ -71,3 +71,35 @@ def test_bond_dimension_search_doubling_then_bisection(monkeypatch):
     assert res["chi"] >= 500 and 10.0 / res["chi"] <= 0.02
     assert all(e > 0.02 for c, e in res["visited"] if c < res["chi"])
     assert len(chis) == 7 + 4
+
+
+def test_transmission_rule():
+    """mu = beta N^gamma / N (Results), refused outside [0, 1]."""
+    import numpy as np
+    import pytest
+    import paper_2301_12814_gb300.experiments as ex
+    mu = ex.transmission([10, 100, 1000], 1.0, 0.5)
+    assert np.allclose(mu, [10 ** -0.5, 0.1, 1000 ** -0.5])
+    assert np.allclose(ex.transmission(50, 0.4, 1.0), 0.4)
+    with pytest.raises(ValueError):
+        ex.transmission(10, 2.0, 1.0)
+
+
+def test_asymptotic_bench_flop_count():
+    """The App. C roofline's algorithmic flops: per block of nb columns and s sweeps,
+    nb(nb-1)/2 pairs x 6 nb for the dot products per sweep plus 6 nb for the rotation
+    in every sweep but the last; the four blocks' sizes add up to (n_max+1)^2."""
+    import os
+    import sys
+    import numpy as np
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = 8
+    L, E = n + 1, n // 2 + 1
+    O = L - E
+    nbs = [E * (E + 1) // 2 + O * (O + 1) // 2, E * O, E * (E - 1) // 2 + O * (O - 1) // 2, E * O]
+    assert sum(nbs) == L * L
+    sweeps = np.array([[3, 2, 1, 4]])
+    want = sum(s * nb * (nb - 1) / 2 * 6 * nb + max(s - 1, 0) * nb * (nb - 1) / 2 * 6 * nb
+               for s, nb in zip(sweeps[0], nbs))
+    assert abs(bench.asym_flops(n, sweeps.ravel()) - want) < 1e-6 * want
