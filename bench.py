@@ -386,9 +386,12 @@ def oracle_asymptotic(n_points: int, repeats: int = 1) -> dict:
 
 
 def asym_flops(n_max: int, sweeps: np.ndarray) -> float:
-    """Algorithmic FP64 flops of the block Jacobi: per visited column pair of a block of
-    nb columns, 6 nb for the three dot products; 6 nb more for the rotation in every
-    sweep but the last (which by definition rotates nothing)."""
+    """Algorithmic FP64 flops of the block Jacobi.  A block of nb columns has
+    nb (nb - 1) / 2 column pairs.  In every sweep each pair costs 6 nb flops for its
+    three dot products (3 FMAs per row).  A rotation costs 6 nb more (per row, two
+    products and two FMAs); every pair is counted as rotated in every sweep but the
+    last, which by definition rotates nothing -- an upper bound on the rotations of
+    the earlier sweeps, since pairs that are already orthogonal skip theirs."""
     L = n_max + 1
     E = n_max // 2 + 1
     O = L - E

@@ -306,9 +306,15 @@ mpo_status mpo_asymptotic_ee_device(int npts, int n_max, const double* r, const 
  *   cuda_stream              stream to run on (NULL = legacy default)
  * Asynchronous: out is ready when the stream reaches this point.  The first call on
  * a device looks up the scratch array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call
- * shares the one scratch array, which keeps the last call's contents (nothing in it
- * needs to start at zero): calls that overlap on the GPU race with each other. */
+ * that device current; make that first call before any stream capture.  The address
+ * is cached with the ID of the device's current CUDA context and looked up again when
+ * that ID changes (for example after cudaDeviceReset); the first call after such a
+ * change must likewise come before any capture.  Every call shares the one scratch
+ * array, which keeps the last call's contents (nothing in it needs to start at zero):
+ * calls that overlap on the GPU race with each other.  The device tables are not
+ * validated on the host: the kernel clamps every size and index it reads from them
+ * (chi to [0, D], pair indices to [0, (n_cap+1)^2), segment offsets to [0, chi]), so
+ * out-of-range values give meaningless numbers, never an out-of-bounds access. */
 mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const int* charge,
                                   const int* segoff, const double* lam, const void* gam,
                                   double* out, void* cuda_stream);

@@ -144,6 +144,15 @@ __host__ __device__ inline int pair_cb(int p, int ncap) { return p % (ncap + 1);
 __host__ __device__ inline int pair_mirror(int p, int ncap) {
   return (p % (ncap + 1)) * (ncap + 1) + p / (ncap + 1);
 }
+// Clamped reads of bond tables that may come from caller-owned device buffers
+// (k_obs): chi to [0, D], a pair index is usable only inside [0, P), and the segment
+// [lo, hi) of pair p to [0, chi] with lo <= hi.  No-ops on valid tables.
+__host__ __device__ inline int clamp_chi(int chi, int D) { return chi < 0 ? 0 : (chi > D ? D : chi); }
+__host__ __device__ inline bool pair_ok(int p, int P) { return p >= 0 && p < P; }
+__host__ __device__ inline void clamp_seg(const int* seg, int p, int chi, int& lo, int& hi) {
+  lo = seg[p] < 0 ? 0 : (seg[p] > chi ? chi : seg[p]);
+  hi = seg[p + 1] < lo ? lo : (seg[p + 1] > chi ? chi : seg[p + 1]);
+}
 __host__ __device__ inline int fock_off(int n) { return n * (n + 1) * (2 * n + 1) / 6; }
 // inverse of canon_pair for a pair with c <= cbar
 __host__ __device__ inline int canon_index(int m, int ncap) {

@@ -8,6 +8,13 @@
 //   F_M = 1,         F_j(a)     = sum_b Gamma_j[a, b] lambda_{j+1}(b) F_{j+1}(b)
 //   Tr rho = E_M,    <n_j^p> Tr rho = sum_{a,b} E_j(a) Gamma_j[a, b] i^p lambda_{j+1}(b) F_{j+1}(b)
 // Sums run over segments: the partners of b are the pairs (c_b + i, cbar_b + i).
+//
+// The bond tables may come from caller-owned device buffers (mpo_observables_static),
+// so every device-read size and index is clamped before use: chi to [0, D], pair
+// indices to [0, P), segment offsets to [0, chi of their bond].  For valid tables the
+// clamps change nothing; for invalid ones the numbers are meaningless but every access
+// stays inside gam, lam, charge and the scratch.
+#include <cuda.h>
 #include <mutex>
 
 #include "../../include/gbs_mpo.h"
@@ -28,6 +35,11 @@ __device__ double2 block_sum2(double2 v, double2* red) {
   return r;
 }
 
+__device__ __forceinline__ int chi_at(const MpoDev& s, long long b) { return clamp_chi(s.chi[b], s.D); }
+__device__ __forceinline__ void seg_at(const int* seg, int p, int chi, int& lo, int& hi) {
+  clamp_seg(seg, p, chi, lo, hi);
+}
+
 __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scratch, double* __restrict__ out) {
   const int inst = blockIdx.x;
   const int M = s.M, D = s.D, P = s.P, ncap = s.ncap, q = ncap + 1;
@@ -38,12 +50,12 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
   double* o = out + (long long)inst * (1 + 2 * M + (M + 1));
   auto bi = [&](int b) { return (long long)inst * (M + 1) + b; };
   {
-    const int chi0 = s.chi[bi(0)];
+    const int chi0 = chi_at(s, bi(0));
     for (int a = tid; a < chi0; a += nth) E[a] = make_double2(s.lam[bi(0) * D + a], 0.0);
   }
   __syncthreads();
   for (int j = 0; j < M; ++j) {
-    const int chiB = s.chi[bi(j + 1)];
+    const int chiA = chi_at(s, bi(j)), chiB = chi_at(s, bi(j + 1));
     const int* chB = s.charge + bi(j + 1) * D;
     const int* segA = s.segoff + bi(j) * (P + 1);
     const double2* G = s.gam + ((long long)inst * M + j) * D * D;
@@ -51,11 +63,15 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
     const double2* Ej = E + (long long)j * D;
     double2* En = E + (long long)(j + 1) * D;
     for (int b = tid; b < chiB; b += nth) {
-      const int pb = chB[b], x = pair_c(pb, ncap), y = pair_cb(pb, ncap);
+      const int pb = chB[b];
       double2 acc = make_double2(0.0, 0.0);
-      for (int i = 0; x + i <= ncap && y + i <= ncap; ++i) {
-        const int pa = (x + i) * q + (y + i);
-        for (int a = segA[pa]; a < segA[pa + 1]; ++a) cfma(acc, Ej[a], G[(long long)a * D + b]);
+      if (pair_ok(pb, P)) {
+        const int x = pair_c(pb, ncap), y = pair_cb(pb, ncap);
+        for (int i = 0; x + i <= ncap && y + i <= ncap; ++i) {
+          int a0, a1;
+          seg_at(segA, (x + i) * q + (y + i), chiA, a0, a1);
+          for (int a = a0; a < a1; ++a) cfma(acc, Ej[a], G[(long long)a * D + b]);
+        }
       }
       En[b] = cscale(acc, lB[b]);
     }
@@ -64,7 +80,7 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
   if (tid == 0) F[(long long)M * D] = make_double2(1.0, 0.0);
   __syncthreads();
   for (int j = M - 1; j >= 0; --j) {
-    const int chiA = s.chi[bi(j)];
+    const int chiA = chi_at(s, bi(j)), chiB = chi_at(s, bi(j + 1));
     const int* chA = s.charge + bi(j) * D;
     const int* segB = s.segoff + bi(j + 1) * (P + 1);
     const double2* G = s.gam + ((long long)inst * M + j) * D * D;
@@ -72,12 +88,15 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
     const double2* Fn = F + (long long)(j + 1) * D;
     double2* Fj = F + (long long)j * D;
     for (int a = tid; a < chiA; a += nth) {
-      const int pa = chA[a], x = pair_c(pa, ncap), y = pair_cb(pa, ncap);
+      const int pa = chA[a];
       double2 acc = make_double2(0.0, 0.0);
-      for (int i = 0; i <= x && i <= y; ++i) {
-        const int pb = (x - i) * q + (y - i);
-        for (int b = segB[pb]; b < segB[pb + 1]; ++b)
-          cfma(acc, G[(long long)a * D + b], cscale(Fn[b], lB[b]));
+      if (pair_ok(pa, P)) {
+        const int x = pair_c(pa, ncap), y = pair_cb(pa, ncap);
+        for (int i = 0; i <= x && i <= y; ++i) {
+          int b0, b1;
+          seg_at(segB, (x - i) * q + (y - i), chiB, b0, b1);
+          for (int b = b0; b < b1; ++b) cfma(acc, G[(long long)a * D + b], cscale(Fn[b], lB[b]));
+        }
       }
       Fj[a] = acc;
     }
@@ -86,7 +105,7 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
   const double tr = E[(long long)M * D].x;
   if (tid == 0) o[0] = tr;
   for (int j = 0; j < M; ++j) {
-    const int chiA = s.chi[bi(j)];
+    const int chiA = chi_at(s, bi(j)), chiB = chi_at(s, bi(j + 1));
     const int* chA = s.charge + bi(j) * D;
     const int* segB = s.segoff + bi(j + 1) * (P + 1);
     const double2* G = s.gam + ((long long)inst * M + j) * D * D;
@@ -95,11 +114,14 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
     const double2* Fn = F + (long long)(j + 1) * D;
     double2 s1 = make_double2(0.0, 0.0), s2 = make_double2(0.0, 0.0);
     for (int a = tid; a < chiA; a += nth) {
-      const int pa = chA[a], x = pair_c(pa, ncap), y = pair_cb(pa, ncap);
+      const int pa = chA[a];
+      if (!pair_ok(pa, P)) continue;
+      const int x = pair_c(pa, ncap), y = pair_cb(pa, ncap);
       double2 acc1 = make_double2(0.0, 0.0), acc2 = make_double2(0.0, 0.0);
       for (int i = 1; i <= x && i <= y; ++i) {
-        const int pb = (x - i) * q + (y - i);
-        for (int b = segB[pb]; b < segB[pb + 1]; ++b) {
+        int b0, b1;
+        seg_at(segB, (x - i) * q + (y - i), chiB, b0, b1);
+        for (int b = b0; b < b1; ++b) {
           const double2 v = cmul(G[(long long)a * D + b], cscale(Fn[b], lB[b]));
           acc1 = cadd(acc1, cscale(v, (double)i));
           acc2 = cadd(acc2, cscale(v, (double)(i * i)));
@@ -114,7 +136,7 @@ __global__ void __launch_bounds__(256) k_obs(MpoDev s, double2* __restrict__ scr
   }
   // purity sum lambda^2 per bond
   for (int b = tid; b <= M; b += nth) {
-    const int chi = s.chi[bi(b)];
+    const int chi = chi_at(s, bi(b));
     double acc = 0.0;
     for (int i = 0; i < chi; ++i) { const double l = s.lam[bi(b) * D + i]; acc += l * l; }
     o[1 + 2 * M + b] = acc;
@@ -143,12 +165,46 @@ void launch_observables(const MpoDev& s, double2* scratch, double* out, cudaStre
 static __device__ __align__(256) double2 g_obs_scratch[MPO_STATIC_SCRATCH_ELEMS];
 
 namespace {
-// Device address of g_obs_scratch per device, looked up once per device (with that
-// device current) by cudaGetSymbolAddress: in host code the symbol's name is only a
-// host-side stand-in, never a device address.
+// Device address of g_obs_scratch per device, looked up by cudaGetSymbolAddress with
+// that device current: in host code the symbol's name is only a host-side stand-in,
+// never a device address.  The address belongs to the device's current CUDA context,
+// so it is cached together with that context's unique ID and looked up again when the
+// ID changes (after cudaDeviceReset the runtime creates a new primary context and
+// loads the module anew).  The driver calls are reached through the runtime's
+// entry-point query, so the library keeps no link-time dependency on libcuda; if the
+// query fails, the address is looked up on every call.
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 double2* g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// ID of the calling thread's current context; false if none is current or the driver
+// calls are unavailable.
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    cudaGetLastError();  // a failed query leaves no sticky error behind
+  }
+  if (!get_cur || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_cur(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 cudaError_t static_scratch(double2** out) {
   int dev = 0;
@@ -156,11 +212,14 @@ cudaError_t static_scratch(double2** out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (g_scratch_ptr[dev] == nullptr || !have_id || id != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_obs_scratch);
+    e = cudaGetSymbolAddress(&p, g_obs_scratch);  // also makes the primary context current
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = static_cast<double2*>(p);
+    g_scratch_ctx[dev] = current_context_id(&id) ? id : 0;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;

@@ -86,20 +86,40 @@ def test_transmission_rule():
 
 
 def test_asymptotic_bench_flop_count():
-    """The App. C roofline's algorithmic flops: per block of nb columns and s sweeps,
-    nb(nb-1)/2 pairs x 6 nb for the dot products per sweep plus 6 nb for the rotation
-    in every sweep but the last; the four blocks' sizes add up to (n_max+1)^2."""
+    """The App. C roofline's flop count, pinned by hand-counted cases.
+
+    Block sizes: the columns (k, k') of X, k, k' = 0..n_max, split into symmetric
+    and antisymmetric combinations under the swap and by the parity of k + k';
+    enumerated here one by one.  Flops: a block of nb columns has nb (nb - 1) / 2
+    pairs; per pair and sweep 3 FMAs per row for the dot products (6 nb flops), and
+    6 nb for a rotation (two products and two FMAs per row) in every sweep but the
+    last.  For n_max = 1 the blocks have 2, 1, 0, 1 columns; with sweeps (3, 2, 1, 4)
+    only the first block has a pair: 3 sweeps x 12 + 2 x 12 = 60 flops.  For
+    n_max = 2 the blocks have 4, 2, 1, 2 columns: 6 pairs x 24 x (3 + 2) = 720,
+    12 x (2 + 1) = 36, 0 and 12 x (4 + 3) = 84, in total 840."""
     import os
     import sys
     import numpy as np
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
-    n = 8
-    L, E = n + 1, n // 2 + 1
-    O = L - E
-    nbs = [E * (E + 1) // 2 + O * (O + 1) // 2, E * O, E * (E - 1) // 2 + O * (O - 1) // 2, E * O]
-    assert sum(nbs) == L * L
-    sweeps = np.array([[3, 2, 1, 4]])
-    want = sum(s * nb * (nb - 1) / 2 * 6 * nb + max(s - 1, 0) * nb * (nb - 1) / 2 * 6 * nb
-               for s, nb in zip(sweeps[0], nbs))
-    assert abs(bench.asym_flops(n, sweeps.ravel()) - want) < 1e-6 * want
+
+    def block_sizes(n_max):
+        sizes = [0, 0, 0, 0]  # sym/even, sym/odd, antisym/even, antisym/odd
+        for k in range(n_max + 1):
+            for kk in range(k, n_max + 1):
+                odd = (k + kk) % 2
+                sizes[0 + odd] += 1
+                if kk > k:
+                    sizes[2 + odd] += 1
+        return sizes
+
+    assert block_sizes(1) == [2, 1, 0, 1]
+    assert block_sizes(2) == [4, 2, 1, 2]
+    for n_max in range(1, 12):
+        assert sum(block_sizes(n_max)) == (n_max + 1) ** 2
+        # a single sweep of each block is its dot products alone
+        want = sum(nb * (nb - 1) / 2 * 6 * nb for nb in block_sizes(n_max))
+        assert abs(bench.asym_flops(n_max, np.ones(4, dtype=int)) - want) <= 1e-9 * max(want, 1.0)
+    sweeps = np.array([3, 2, 1, 4])
+    assert bench.asym_flops(1, sweeps) == 60.0
+    assert bench.asym_flops(2, sweeps) == 840.0

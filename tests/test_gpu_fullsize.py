@@ -1,0 +1,172 @@
+"""GPU parity at the large workloads' full sizes, against the oracle's stored results.
+
+tests/golden/mesh_<workload>.json hold what the FP64 oracle (App. D: Eq. `theta`,
+LAPACK SVD per block, keep chi, Vidal re-split) computes on the workload's Clements
+mesh from the initial state: after a prefix of gates (and after the whole mesh, with
+the final phase screen) Tr rho, <n_j>, <n_j^2>, the entropy and purity at every cut,
+the bond dimensions and the largest bond weights, plus the discarded weight of every
+gate.  They are written by tests/golden/make_mesh_goldens.py, which calls only the
+oracle and the seeded input generators.
+
+* FP64 path: every observable within 1e-10 relative (absolute floor 1e-12), the
+  bond dimensions identical, the largest bond weights within 1e-10 of the bond's
+  largest, the per-gate discarded weights within 1e-10 relative to the largest.
+  Runs: the whole 32-mode chi = 256 mesh (496 gates + phases); the 48-mode
+  chi = 512 mesh after 24 and 60 gates (every bond the gates touch reaches 512; the
+  largest Theta(m) has a Gram side of several hundred, so the cluster route runs
+  with w > 1 column blocks per CTA) and the whole 1128-gate mesh.
+* Mixed path: the per-observable bounds stated for it -- on prefixes 1e-4 relative
+  (<n>, <n^2>), 1e-3 absolute (S), 1e-4 absolute (Tr), 1e-2 relative to the largest
+  (discarded weight); on whole meshes at chi >= 256, where FP32 rounding can swap two
+  nearly equal singular values across the chi cut, 5e-2, 1e-2, 2e-3 and 1e-1.
+  Runs: the same meshes, and four instances of the 64-instance batched workload run
+  together in one handle against the oracle run live on each.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gbs_workloads as w
+from oracle import u1mpo
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+RTOL, ATOL = 1e-10, 1e-12
+MIXED_PREFIX = dict(n=1e-4, n2=1e-4, S=1e-3, tr=1e-4, eps=1e-2)
+MIXED_WHOLE = dict(n=5e-2, n2=5e-2, S=1e-2, tr=2e-3, eps=1e-1)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2301_12814_gb300 import build, mpo
+    mpo.load_library(build.build())
+    return mpo
+
+
+def golden(name):
+    with open(os.path.join(HERE, "golden", f"mesh_{name}.json")) as f:
+        return json.load(f)
+
+
+def snap(g, n):
+    for s in g["snapshots"]:
+        if s["gates"] == n:
+            return s
+    raise KeyError(n)
+
+
+def run_gpu(lib, name, n, precision):
+    """The first n gates of the workload's mesh (with the phase screen when n is the
+    whole mesh) as a CUDA-graph plan, the launch configuration the benchmark times."""
+    wl = w.workload(name)
+    mesh = wl.mesh(0)
+    G = lib.MPO(wl.M, wl.d, wl.r[0], wl.eta[0], chi_max=wl.chi, precision=precision)
+    fp = mesh.final_phase if n == mesh.n_gates else None
+    plan = G.plan_mesh([n], mesh.k[:n], mesh.theta[:n], mesh.phi[:n], fp)
+    plan.run()
+    disc = plan.discarded()
+    tr, n1, n2 = G.observables()
+    S, pur, _ = G.operator_entropy()
+    chi, lams, _ = G.bonds(0)
+    G.close()
+    return dict(trace=tr[0], n_mean=n1[0], n2_mean=n2[0], entropy=S[0], purity=pur[0], chi=np.asarray(chi),
+                lams=lams, discarded=np.asarray(disc))
+
+
+def close(a, b, rtol=RTOL, atol=ATOL):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    return bool(np.all(np.abs(a - b) <= atol + rtol * np.abs(b)))
+
+
+def check_fp64(got, s, disc_ref):
+    assert close(got["trace"], s["trace"]), (got["trace"], s["trace"])
+    for key in ("n_mean", "n2_mean", "entropy", "purity"):
+        a, b = np.asarray(got[key]), np.asarray(s[key])
+        assert close(a, b), (key, float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))))
+    assert list(got["chi"]) == s["chi"]
+    for b, top in enumerate(s["lam_top"]):
+        lg = np.sort(np.asarray(got["lams"][b]))[::-1][:len(top)]
+        assert np.all(np.abs(lg - np.asarray(top)) <= 1e-10 * top[0]), b
+    d = np.asarray(disc_ref[:len(got["discarded"])])
+    assert np.all(np.abs(got["discarded"] - d) <= 1e-10 * max(float(np.max(d)), 1e-300) + 1e-15)
+
+
+def mixed_errors(got, s, disc_ref):
+    rel = lambda x, y: float(np.max(np.abs(np.asarray(x) - np.asarray(y)) / np.abs(np.asarray(y))))
+    d = np.asarray(disc_ref[:len(got["discarded"])])
+    return dict(n=rel(got["n_mean"], s["n_mean"]), n2=rel(got["n2_mean"], s["n2_mean"]),
+                S=float(np.max(np.abs(np.asarray(got["entropy"]) - np.asarray(s["entropy"])))),
+                tr=abs(got["trace"] - s["trace"]),
+                eps=float(np.max(np.abs(got["discarded"] - d)) / max(float(np.max(d)), 1e-300)))
+
+
+def check_mixed(got, s, disc_ref, bounds):
+    err = mixed_errors(got, s, disc_ref)
+    for k, v in bounds.items():
+        assert err[k] <= v, (k, err[k], v, err)
+    assert got["trace"] <= 1.0 + 1e-6
+    return err
+
+
+def test_M32_chi256_whole_mesh_fp64(lib):
+    g = golden("M32_d8_chi256")
+    n = g["n_gates_mesh"]
+    check_fp64(run_gpu(lib, "M32_d8_chi256", n, "fp64"), snap(g, n), g["discarded"])
+
+
+@pytest.mark.parametrize("n", [24, 60])
+def test_M48_chi512_prefix_fp64(lib, n):
+    g = golden("M48_d8_chi512")
+    s = snap(g, n)
+    assert max(s["chi"]) == 512
+    assert s["largest_block"]["gram_side"] >= 128
+    check_fp64(run_gpu(lib, "M48_d8_chi512", n, "fp64"), s, g["discarded"])
+
+
+def test_M48_chi512_whole_mesh_fp64(lib):
+    g = golden("M48_d8_chi512")
+    n = g["n_gates_mesh"]
+    check_fp64(run_gpu(lib, "M48_d8_chi512", n, "fp64"), snap(g, n), g["discarded"])
+
+
+@pytest.mark.parametrize("name,n,bounds", [
+    ("M32_d8_chi256", 120, MIXED_PREFIX),
+    ("M32_d8_chi256", 496, MIXED_WHOLE),
+    ("M48_d8_chi512", 24, MIXED_PREFIX),
+    ("M48_d8_chi512", 1128, MIXED_WHOLE),
+])
+def test_mixed_vs_oracle(lib, name, n, bounds):
+    g = golden(name)
+    check_mixed(run_gpu(lib, name, n, "mixed_tf32"), snap(g, n), g["discarded"], bounds)
+
+
+def test_batched_mixed_instances_vs_oracle(lib):
+    """Four instances of the 64-instance batched workload (their own r, eta, chi and
+    Haar mesh) run together in one handle on the mixed path; each is compared with
+    the oracle run on its own at the prefix bounds."""
+    wl = w.workload("batched_64x_M16_d6")
+    insts = [0, 17, 42, 63]
+    meshes = [wl.mesh(i) for i in insts]
+    G = lib.MPO(wl.M, wl.d, np.stack([wl.r[i] for i in insts]), np.stack([wl.eta[i] for i in insts]),
+                chi_max=[wl.chis[i] for i in insts], batch=len(insts), precision="mixed_tf32")
+    n_gates = [m.n_gates for m in meshes]
+    disc = G.sweep_mesh(n_gates, np.concatenate([m.k for m in meshes]), np.concatenate([m.theta for m in meshes]),
+                        np.concatenate([m.phi for m in meshes]), np.concatenate([m.final_phase for m in meshes]))
+    tr, n1, n2 = G.observables()
+    S, pur, _ = G.operator_entropy()
+    off = np.concatenate([[0], np.cumsum(n_gates)])
+    for b, i in enumerate(insts):
+        P = u1mpo.U1MPO(wl.M, wl.d, wl.r[i], wl.eta[i], chi_max=wl.chis[i])
+        P.run_mesh(meshes[b].k, meshes[b].theta, meshes[b].phi, meshes[b].final_phase)
+        otr, on1, on2 = P.observables()
+        s = dict(trace=otr, n_mean=on1, n2_mean=on2, entropy=P.entropy)
+        got = dict(trace=tr[b], n_mean=n1[b], n2_mean=n2[b], entropy=S[b],
+                   discarded=np.asarray(disc[off[b]:off[b + 1]]))
+        check_mixed(got, s, P.discarded, MIXED_PREFIX)
+    G.close()

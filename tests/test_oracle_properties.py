@@ -11,11 +11,30 @@ import math
 import numpy as np
 import pytest
 
-hyp = pytest.importorskip("hypothesis")
-st = pytest.importorskip("hypothesis.strategies")
-from hypothesis import given, settings  # noqa: E402
+from oracle import fock
 
-from oracle import fock  # noqa: E402
+try:
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+except ImportError:
+    # Without hypothesis each test skips on its own.  A module-level skip would be
+    # reported as a skipped test even in runs that deselect this CPU-only file.
+    class _NoStrategies:
+        def __getattr__(self, name):
+            return lambda *a, **k: None
+
+    st = _NoStrategies()
+
+    def settings(**kwargs):
+        return lambda f: f
+
+    def given(**kwargs):
+        def wrap(f):
+            def skipped():
+                pytest.skip("hypothesis is not installed")
+            skipped.__name__, skipped.__doc__ = f.__name__, f.__doc__
+            return skipped
+        return wrap
 
 
 def _u2(a, b, c, d):
