@@ -33,10 +33,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "beam-splitter MPO updates/s at (M,d,chi); mixed vs FP64 at stated observable error"
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (non-tensor = tensor) nominal: 152 SMs x 2.07 GHz x ~4 flop/clk
+DEFAULT_WORKLOAD = "M48_d8_chi512"
+# nominal figures, used only when the live measurement (mpo_measure_peaks) fails
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2.07 GHz x ~4 flop/clk
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 2.07 GHz x 128 FMA (256 flop) per clock
 ORACLE_SAMPLE_GATES = {"exact_M4_d4": 6, "M16_d6_chi64": 120, "M32_d8_chi256": 12,
-                       "batched_64x_M16_d6": 60, "M48_d8_chi512": 6}
+                       "batched_64x_M16_d6": 60, "M48_d8_chi512": 24}
+# tensor-pipe passes per real product of the contraction kernel, by path
+MMA_PASSES = {"mixed_tf32": 3, "mixed_bf16": 1}
+
+
+def measured_peaks() -> dict:
+    """FP64/FP32 FMA and TF32/BF16 tcgen05 peaks of this GPU, measured now (best of
+    three), with MEASURED_PEAKS.json's measured HBM and cuBLAS bf16 beside."""
+    import paper_2301_12814_gb300 as lib
+    out = {"source": "mpo_measure_peaks (FMA chains; tcgen05.mma on smem operands), best of 3"}
+    try:
+        runs = [lib.mpo.measure_peaks() for _ in range(3)]
+        for k in ("fp64", "fp32", "tf32", "bf16"):
+            out[k] = max(r[k] for r in runs)
+    except Exception as e:  # never lose the line over the probe
+        out.update(fp64=FP64_PEAK_TFLOPS, fp32=FP32_PEAK_TFLOPS, tf32=None, bf16=None,
+                   source=f"nominal (probe failed: {str(e)[-120:]})")
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        out["hbm_gbs"] = mp.get("hbm_gbs")
+        out["bf16_cublas"] = mp.get("bf16_tflops")
+    except (OSError, ValueError):
+        pass
+    return out
 
 
 def _dist():
@@ -175,33 +201,56 @@ def observable_errors(a, b) -> dict:
             "eps_rel": float(np.max(np.abs(d_a - d_b)) / max(float(np.max(np.abs(d_b))), 1e-300))}
 
 
-def compare_precision(args, wl, meshes, prec, n_gates, k, th, ph, fp, obs, stream):
-    """The same workload on the other path (mixed <-> FP64): its updates/s (graph
-    replays timed with CUDA events, a few steps) and the observable errors of the
-    mixed run against the FP64 run."""
+def compare_precision(args, wl, n_gates, k, th, ph, fp, obs, stream, other, peaks):
+    """The same workload on another path: its updates/s (graph replays timed with
+    CUDA events, a few steps), its per-stage device times, the observable errors of
+    the mixed run against the FP64 run, and the tensor-pipe roofline of its
+    contraction kernel (F_Theta flops of Eq. `theta` / its device time)."""
     import torch
     import paper_2301_12814_gb300 as lib
-    other = "mixed_tf32" if prec == "fp64" else "fp64"
     G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=other, stream=stream)
     plan = G.plan_mesh(n_gates, k, th, ph, fp)
     G.reset(); plan.run()
     steps = max(1, min(args.steps, 5))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = 0.0
+    live = {s_: 0.0 for s_ in lib.mpo.Plan.STAGES}
     for _ in range(steps):
         G.reset()
         e0.record(stream); plan.run(); e1.record(stream)
         e1.synchronize()
         ms += e0.elapsed_time(e1)
+        for s_, v in plan.stage_times().items():
+            live[s_] += v / steps
     disc = plan.discarded()
     tr, n1, n2 = G.observables()
     S, _, _ = G.operator_entropy()
+    G.reset()
+    prof, jac = plan.profile(with_jacobi=True)
     G.close()
-    mine = obs
-    theirs = (tr, n1, n2, S, disc)
-    mixed, fp64 = (theirs, mine) if prec == "fp64" else (mine, theirs)
-    return {"precision": other, "value": int(sum(n_gates)) * steps / (ms / 1e3), "unit": "updates/s",
-            "steps": steps, "mixed_vs_fp64": observable_errors(mixed, fp64)}
+    out = {"precision": other, "value": int(sum(n_gates)) * steps / (ms / 1e3), "unit": "updates/s",
+           "steps": steps, "stages_ms": {s_: round(v, 4) for s_, v in live.items()}}
+    if other != "fp64":
+        out["mixed_vs_fp64"] = observable_errors((tr, n1, n2, S, disc), obs)
+        fth = jac["theta_F_flops"]
+        t_ms = live["theta"]
+        peak = peaks.get("tf32" if other == "mixed_tf32" else "bf16")
+        ach = fth / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+        passes = MMA_PASSES.get(other, 1)
+        out["contraction_roofline"] = {
+            "kernel": "k_theta_tc", "bound": "tensor", "unit": "TFLOP/s",
+            "algorithmic_flops_per_step": fth, "achieved": ach, "peak": peak,
+            "frac": ach / peak if peak else None,
+            "tensor_pipe_frac": passes * ach / peak if peak else None,
+            "mma_passes": passes,
+            "peak_source": f"{'TF32' if other == 'mixed_tf32' else 'BF16'} tcgen05 peak measured in this run",
+            "note": "frac = F_Theta / stage time / peak; tensor_pipe_frac counts the MMA passes of the split "
+                    "(3xTF32: 3 products per real product), not the padding of partial tiles"}
+        out["jacobi"] = {"cluster_blocks": jac["cluster_blocks"],
+                         "cluster_ms_per_block": jac["cluster_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6,
+                         "cluster_ms_split": {k_: jac[f"cluster_{k_}_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6
+                                              for k_ in ("seed", "ns", "polish")}}
+    return out
 
 
 def run_native(args, ws, rank, local):
@@ -228,6 +277,7 @@ def run_native(args, ws, rank, local):
     fp = np.concatenate([m.final_phase for m in meshes])
     units = int(sum(n_gates))
     stream = torch.cuda.Stream(device=dev)
+    peaks = measured_peaks()
     G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=prec, stream=stream)
     plan = G.plan_mesh(n_gates, k, th, ph, fp)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -276,7 +326,7 @@ def run_native(args, ws, rank, local):
     prof, jac = plan.profile(with_jacobi=True)
     # end to end through the public API with host buffers
     e2e_t = []
-    for i in range(max(1, args.steps)):
+    for i in range(max(1, min(args.steps, 2))):
         t0 = time.perf_counter()
         G.reset()
         d_host = G.sweep_mesh(n_gates, k, th, ph, fp)
@@ -300,20 +350,29 @@ def run_native(args, ws, rank, local):
     _, nl_s, fl_s = prof[stage]
     ms_s = live_step[stage]
     fp64_stage = prec == "fp64" and stage in ("theta", "svd")
+    fl32 = 0.0
     if stage == "svd" and prec == "fp64":
         fl_s = jac["refine_flops"]  # the FP64 part; the FP32 seed is reported beside it
-    peak = FP64_PEAK_TFLOPS if fp64_stage else FP32_PEAK_TFLOPS
+        fl32 = jac["seed_flops"]
+    peak = peaks["fp64"] if fp64_stage else peaks["fp32"]
     achieved = fl_s / (ms_s / 1e3) / 1e12 if ms_s > 0 else 0.0
     roofline = {"bound": "alu", "kernel": f"k_{stage}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": ("FP64" if fp64_stage else "FP32") + " SIMT FMA peak derived from 152 SMs x "
-                               "2.07 GHz (FP64 4, FP32 256 flop/clk/SM); MEASURED_PEAKS.json has only HBM and "
-                               "bf16 tensor peaks",
+                "peak_source": ("FP64" if fp64_stage else "FP32") + " FMA-chain peak measured in this run "
+                               "(mpo_measure_peaks)",
                 "traffic": None, "flops_per_launch": fl_s / max(1, nl_s),
                 "avg_launch_ms": ms_s / max(1, nl_s), "launches_per_step": nl_s,
                 "timing": "CUDA event record nodes inside the replayed graph, timed steps only"}
-    compare = None if args.no_compare else compare_precision(args, wl, meshes, prec, n_gates, k, th, ph, fp,
-                                                            (tr, n1, n2, S, disc), stream)
+    if fl32 > 0:
+        # both pipes the kernel uses: the time the FP64 refinement and the FP32 seed
+        # would take at their measured peaks, against the kernel's time
+        roofline["fp32_seed_flops_per_launch"] = fl32 / max(1, nl_s)
+        roofline["two_pipe_frac"] = (fl_s / (peaks["fp64"] * 1e12) + fl32 / (peaks["fp32"] * 1e12)) / (ms_s / 1e3)
+    compare = None
+    if not args.no_compare:
+        others = ["mixed_tf32", "mixed_bf16"] if prec == "fp64" else ["fp64"]
+        compare = [compare_precision(args, wl, n_gates, k, th, ph, fp, (tr, n1, n2, S, disc), stream, o, peaks)
+                   for o in others]
     # CPU oracle on a bounded sample (host cores, single BLAS thread)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -351,6 +410,8 @@ def run_native(args, ws, rank, local):
         "compare": compare,
         "stages_ms": {s_: round(v, 4) for s_, v in live_step.items()},
         "stages_gflop": {s: round(v[2] / 1e9, 4) for s, v in prof.items() if v[2] > 0},
+        "theta_F_gflop": round(jac["theta_F_flops"] / 1e9, 4),
+        "peaks_tflops": peaks,
         "jacobi": {"blocks": jac["blocks"], "sweeps_per_block": jac["sweeps"] / max(1, jac["blocks"]),
                    "refine_sweeps_per_block": jac["refine_sweeps"] / max(1, jac["blocks"]),
                    "seed_gflop_fp32": jac["seed_flops"] / 1e9, "refine_gflop": jac["refine_flops"] / 1e9,
@@ -535,11 +596,12 @@ def run_asymptotic(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="M16_d6_chi64")
-    ap.add_argument("--precision", default=None)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--precision", default="fp64",
+                    help="path timed as `value` (fp64, mixed_tf32, mixed_bf16); the others go to `compare`")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the run on the other precision")
     args = ap.parse_args()

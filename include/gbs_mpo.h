@@ -45,7 +45,8 @@ typedef enum {
   MPO_ERR_OOM = 2,       /* device allocation failed                             */
   MPO_ERR_CUDA = 3,      /* a CUDA runtime call failed                           */
   MPO_ERR_NUMERIC = 4,   /* eigensolver sweep cap reached or a non-finite value  */
-  MPO_ERR_TIMEOUT = 5,   /* reserved: a bounded device wait ran out              */
+  MPO_ERR_TIMEOUT = 5,   /* a bounded device wait ran out (a tensor-core kernel's
+                            wait for its own MMAs, or the peak probe's)             */
   MPO_ERR_CAPACITY = 6,  /* a workspace bound was exceeded on device: the layer's
                             pools of Theta- and Gram-sized arrays (sized at most to
                             GBS_MPO_WORKSPACE_GB, else a quarter of the free device
@@ -149,18 +150,22 @@ int mpo_plan_launches(mpo_plan p);
 /* Replay the plan once without the graph, with a CUDA event between consecutive
  * stage launches on the handle's stream, and report per stage (setup, theta, gram,
  * order, svd, select, resplit, phases) the summed device time in ms, the launch
- * count and the real flops of the executed form (theta: complex MACs of Eq. `theta`
- * over the contracted blocks x 8; gram: upper triangle x 8 x inner size; svd: FP32
+ * count and the real flops of the executed form (theta, FP64 path: the two-stage SIMT
+ * form, 8 n_a n_b (sum_c n_c + n_c n_m) per row/column segment pair; TF32 and BF16
+ * paths: the one-stage Eq. `theta` on the tensor cores, F_Theta below; gram: upper
+ * triangle x 8 x inner size; svd: FP32
  * seed Jacobi, per applied rotation 54 n (complex) or 18 n (real), plus the
  * refinement, W = Theta V and 48 h + 24 n per applied one-sided rotation, in the
  * path's precision; resplit: element copies).  Each array
- * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [13]): blocks
+ * is [MPO_NSTAGES] host memory and nullable.  jacobi (nullable, [14]): blocks
  * factorised, seed sweeps (two-sided, or the FP32 phase of a cluster block),
  * refinement sweeps, seed flops (FP32), refinement flops (path precision), blocks
  * factorised on a CTA cluster, SM clock cycles spent on cluster blocks (first CTA
  * of the cluster) and on single-CTA blocks, the cluster blocks' cycles in their
  * seed (or FP32 phase), Newton-Schulz and final sweeps, and the blocks factorised
- * by one warp and their cycles, summed over the replay.
+ * by one warp and their cycles, summed over the replay; then F_Theta, the real flops
+ * of Eq. `theta` in one stage over the canonical blocks, sum over m, a >= m >= b and
+ * a >= c >= b of 8 n_a n_c n_b (whatever form ran).
  * Same results as mpo_plan_run.  Synchronises. */
 mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches,
                             double* stage_flops, double* jacobi);
@@ -318,6 +323,18 @@ mpo_status mpo_asymptotic_ee_device(int npts, int n_max, const double* r, const 
 mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const int* charge,
                                   const int* segoff, const double* lam, const void* gam,
                                   double* out, void* cuda_stream);
+
+/* Measured arithmetic peaks of the current GPU, for roofline denominators (a
+ * measurement utility; the paper has no counterpart).  tflops[4] (host) receives, in
+ * TFLOP/s: FP64 FMA, FP32 FMA (8 independent FMA chains per thread, 8 CTAs of 256
+ * threads per SM), TF32 and BF16 tensor-core MMA (tcgen05.mma M = 128, N = 256 on
+ * operands resident in shared memory, FP32 accumulation in TMEM, one CTA per SM);
+ * ms[4] (host, nullable) the timed launch durations.  One warm-up and one timed
+ * launch each, with CUDA events, on the legacy default stream (synchronous; about
+ * 0.1 s in all).  Allocates and frees a few KB of device memory.  MPO_ERR_NOT_BUILT
+ * without a GPU, MPO_ERR_TIMEOUT if a tensor-core wait ran out, MPO_ERR_CUDA /
+ * MPO_ERR_OOM otherwise. */
+mpo_status mpo_measure_peaks(double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

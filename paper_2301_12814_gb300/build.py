@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbsmpo.so")
-SOURCES = ["api.cu", "init.cu", "gate.cu", "obs.cu", "asym.cu"]
+SOURCES = ["api.cu", "init.cu", "gate.cu", "obs.cu", "asym.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
@@ -42,7 +42,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of libgbsmpo.so."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "mpo_internal.cuh"), os.path.join(ROOT, "include", "gbs_mpo.h")]
+    headers = [os.path.join(CSRC, "mpo_internal.cuh"), os.path.join(CSRC, "tc.cuh"),
+               os.path.join(ROOT, "include", "gbs_mpo.h")]
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

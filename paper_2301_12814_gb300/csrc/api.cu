@@ -669,7 +669,8 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
                                   (double)(ctr[CTR_EIG] + ctr[CTR_REFINE]), 0.0, (double)ctr[CTR_RESPLIT], 0.0};
   for (int st = 0; st < MPO_NSTAGES; ++st) {
     if (stage_ms) stage_ms[st] = ms[st];
-    if (stage_launches) stage_launches[st] = st < NS ? L : (p->d_phase ? 1 : 0);
+    // the Gram stage is two launches per layer (SIMT blocks, tensor-core blocks)
+    if (stage_launches) stage_launches[st] = st < NS ? (st == 2 ? 2 * L : L) : (p->d_phase ? 1 : 0);
     if (stage_flops) stage_flops[st] = fl[st];
   }
   if (jacobi) {
@@ -686,6 +687,7 @@ mpo_status mpo_plan_profile(mpo_plan p, double* stage_ms, int* stage_launches, d
     jacobi[10] = (double)ctr[CTR_CYC_POLISH];
     jacobi[11] = (double)ctr[CTR_NWARP];
     jacobi[12] = (double)ctr[CTR_CYC_WARP];
+    jacobi[13] = (double)ctr[CTR_FTHETA];
   }
   return poll_error(h);
 }

@@ -42,6 +42,7 @@
 #include <cstdlib>
 
 #include "mpo_internal.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -587,7 +588,7 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
   const double2* G2 = G1 + (long long)D * D;
   C* Th = reinterpret_cast<C*>(sl.theta);
   const int nitems = sl.scal[SS_TTILES];
-  unsigned long long flops = 0;
+  unsigned long long flops = 0, fth = 0;  // executed two-stage form; one-stage F_Theta
   // large items: the whole CTA per item (lists in warp 0's area, the Gamma tiles in
   // the CTA's P buffers)
   int* shn = reinterpret_cast<int*>(tsm + TL.misc);  // [0] nc, [1] nm of the current large item
@@ -675,6 +676,7 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
       unsigned long long kc = 0;
       for (int ci = 0; ci < nc; ++ci) kc += (unsigned long long)(segC[ccl[ci] + 1] - segC[ccl[ci]]);
       flops += 8ull * (unsigned long long)nent * (kc + (unsigned long long)nc * nm);
+      fth += 8ull * (unsigned long long)nent * kc * (unsigned long long)nm;
     }
     __syncthreads();  // lists and accumulators are reused by the next item
   }
@@ -742,9 +744,225 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
       unsigned long long kc = 0;
       for (int ci = 0; ci < nc; ++ci) kc += (unsigned long long)(segC[clist[ci] + 1] - segC[clist[ci]]);
       flops += 8ull * (unsigned long long)nent * (kc + (unsigned long long)nc * nm);
+      fth += 8ull * (unsigned long long)nent * kc * (unsigned long long)nm;
     }
   }
   if (st.ctr && lane == 0 && flops) atomicAdd(st.ctr + CTR_THETA, flops);
+  if (st.ctr && lane == 0 && fth) atomicAdd(st.ctr + CTR_FTHETA, fth);
+}
+
+// ---------------------------------------------------------------- k_theta_tc
+// Eq. `theta` on the tensor cores (tcgen05, see tc.cuh), for the TF32 and BF16 paths.
+// A work item is (canonical block m, a tile of 128 rows of Theta(m), one column
+// segment b of Theta(m), up to 64 of its columns).  For fixed m and b the weight
+// u(a, b, c, m) of a row alpha (charge a) and a centre index gamma (charge c) is a
+// function of (a, c) alone, so it is folded into the A operand while staging:
+//   A[alpha, gamma] = u(a, b, c, m) Gamma_j[alpha, gamma]      (0 unless a >= c >= b)
+//   B[beta, gamma]  = lambda_C[gamma] Gamma_{j+1}[gamma, beta]
+//   Theta(m)[alpha, beta] = lambda_A[alpha] lambda_B[beta] sum_gamma A B  (epilogue)
+// K runs over the centre indices whose charge dominates b (a gathered list of
+// segments; per stage, a table of the 32 indices' bond positions and charges).  Each
+// item writes every entry of its region of Theta(m), zeros included.  This is the
+// one-stage form of Eq. `theta` (flops F_Theta, counted per row over the c between
+// a and b); the FP64 path keeps the SIMT two-stage kernel.
+constexpr int THETA_TN = 64;
+// Dynamic shared memory of k_theta_tc (byte offsets; the Fock table is sized for the
+// handle's n_cap).  At least 80 KB, so that at most two CTAs share an SM (two TMEM
+// allocations of 256 columns); up to n_cap = 12 it stays within 113 KB, so that two do.
+struct ThetaTcSmem {
+  size_t fk, seg, bpre, clist, cpre, rinfo, kinfo, misc, total;
+};
+template <int MODE>
+__host__ __device__ inline ThetaTcSmem theta_tc_smem(int ncap) {
+  ThetaTcSmem L;
+  const size_t stage = tc::CTile<MODE>::stage_bytes(THETA_TN);
+  L.fk = (stage + 1023) & ~(size_t)1023;
+  L.seg = align16(L.fk + (size_t)fock_off(ncap + 1) * sizeof(float2));
+  L.bpre = L.seg + 3 * (size_t)(MPO_P_MAX + 1) * sizeof(int);
+  L.clist = L.bpre + (size_t)(MPO_PC_MAX + 1) * sizeof(int);
+  L.cpre = L.clist + (size_t)MPO_P_MAX * sizeof(int);
+  L.rinfo = align16(L.cpre + (size_t)(MPO_P_MAX + 1) * sizeof(int));
+  L.kinfo = L.rinfo + 128 * sizeof(int4);
+  L.misc = L.kinfo + 32 * sizeof(int4);
+  const size_t used = L.misc + 64;
+  L.total = used > 80 * 1024 ? used : 80 * 1024;
+  return L;
+}
+
+// Number of column tiles of segment width nb (tiles of up to THETA_TN columns).
+__device__ __forceinline__ int theta_ntiles(int nb) { return (nb + THETA_TN - 1) / THETA_TN; }
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_theta_tc(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates) {
+  extern __shared__ __align__(1024) unsigned char ttsm[];
+  const ThetaTcSmem L = theta_tc_smem<MODE>(st.ncap);
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int s = blockIdx.y;
+  Slot sl = get_slot(ws, s);
+  if (sl.scal[SS_STATUS]) return;
+  const GateDesc g = gates[s];
+  const int ncap = st.ncap, P = st.P, M = st.M, D = st.D, Pc = ws.Pc;
+  const int tid = threadIdx.x;
+  float2* fk = reinterpret_cast<float2*>(ttsm + L.fk);
+  int* segA = reinterpret_cast<int*>(ttsm + L.seg);
+  int* segC = segA + (MPO_P_MAX + 1);
+  int* segB = segC + (MPO_P_MAX + 1);
+  int* bpre = reinterpret_cast<int*>(ttsm + L.bpre);
+  int* clist = reinterpret_cast<int*>(ttsm + L.clist);
+  int* cpre = reinterpret_cast<int*>(ttsm + L.cpre);
+  int4* rinfo = reinterpret_cast<int4*>(ttsm + L.rinfo);
+  int4* kinfo = reinterpret_cast<int4*>(ttsm + L.kinfo);
+  int* misc = reinterpret_cast<int*>(ttsm + L.misc);
+  const long long bA = (long long)g.inst * (M + 1) + g.j, bC = bA + 1, bB = bA + 2;
+  for (int p = tid; p <= P; p += blockDim.x) {
+    segA[p] = st.segoff[bA * (P + 1) + p];
+    segC[p] = st.segoff[bC * (P + 1) + p];
+    segB[p] = st.segoff[bB * (P + 1) + p];
+  }
+  for (int e = tid; e < fock_off(ncap + 1); e += blockDim.x) fk[e] = cvt<float2>(sl.fock[e]);
+  __syncthreads();
+  // items per block: row tiles x (column tiles over the block's column segments)
+  for (int t = tid; t < Pc; t += blockDim.x) {
+    int n = 0;
+    if (sl.f(BF_G, t) > 0) {
+      int ct = 0;
+      for (int b = 0; b < P; ++b)
+        if (sl.coloff[t * P + b] >= 0) ct += theta_ntiles(segB[b + 1] - segB[b]);
+      n = ((sl.f(BF_R, t) + 127) / 128) * ct;
+    }
+    bpre[t + 1] = n;
+  }
+  if (tid == 0) bpre[0] = 0;
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < Pc; ++t) bpre[t + 1] += bpre[t];
+  __syncthreads();
+  const int nitems = bpre[Pc];
+  if ((int)blockIdx.x >= nitems) return;  // CTA-uniform, before any TMEM is held
+  constexpr uint32_t NCOL = tc::CTile<MODE>::tmem_cols(THETA_TN);
+  if (tid < 32) tc::tmem_alloc(&tslot, NCOL);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  tc::Engine E{tslot, &bar, 0u, st.err};
+  const double* lA = st.lam + bA * D;
+  const double* lC = st.lam + bC * D;
+  const double* lB = st.lam + bB * D;
+  const int* chA = st.charge + bA * D;
+  const double2* G1 = st.gam + ((long long)g.inst * M + g.j) * D * D;
+  const double2* G2 = G1 + (long long)D * D;
+  float2* Th = reinterpret_cast<float2*>(sl.theta);
+  unsigned long long flops = 0;
+  for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
+    const int t = find_block(bpre, Pc + 1, z);
+    int rem = z - bpre[t];
+    const int m = sl.f(BF_M, t), cm = pair_c(m, ncap), cbm = pair_cb(m, ncap);
+    const int R = sl.f(BF_R, t), Ccols = sl.f(BF_C, t);
+    int ct = 0;
+    for (int b = 0; b < P; ++b)
+      if (sl.coloff[t * P + b] >= 0) ct += theta_ntiles(segB[b + 1] - segB[b]);
+    const int ti = rem / ct;
+    rem -= ti * ct;
+    int b = 0;
+    for (; b < P; ++b) {
+      if (sl.coloff[t * P + b] < 0) continue;
+      const int nt = theta_ntiles(segB[b + 1] - segB[b]);
+      if (rem < nt) break;
+      rem -= nt;
+    }
+    const int cb = pair_c(b, ncap), cbb = pair_cb(b, ncap);
+    const int n0 = rem * THETA_TN, nbt = min(THETA_TN, segB[b + 1] - segB[b] - n0);
+    const int beta0 = segB[b] + n0, col0 = sl.coloff[t * P + b] + n0, r0 = ti * 128;
+    // centre segments c >= b (the K list) and their prefix
+    if (tid == 0) {
+      int nc = 0, kk = 0;
+      for (int cc = 0; cc < P; ++cc) {
+        if (segC[cc + 1] == segC[cc]) continue;
+        if (pair_c(cc, ncap) < cb || pair_cb(cc, ncap) < cbb) continue;
+        clist[nc] = cc;
+        cpre[nc] = kk;
+        kk += segC[cc + 1] - segC[cc];
+        ++nc;
+      }
+      cpre[nc] = kk;
+      misc[0] = nc;
+    }
+    // rows: bond-A index, charges of a and the Fock row offsets of the weight
+    if (tid < 128) {
+      const int r = r0 + tid;
+      int4 ri = make_int4(-1, 0, 0, 0);
+      if (r < R) {
+        const int alpha = sl.rowmap[sl.f(BF_RMOFF, t) + r];
+        const int pa = chA[alpha], ca = pair_c(pa, ncap), cba = pair_cb(pa, ncap);
+        const int dk = ca - cb, db = cba - cbb;
+        ri.x = alpha;
+        ri.y = ca | (cba << 8);
+        ri.z = fock_off(dk) + (ca - cm) * (dk + 1) + ca;    // + (-c_c): U_dk[ca - cm, ca - c_c]
+        ri.w = fock_off(db) + (cba - cbm) * (db + 1) + cba;  // + (-cbar_c)
+      }
+      rinfo[tid] = ri;
+    }
+    __syncthreads();
+    const int nc = misc[0], K = cpre[nc];
+    if (st.ctr && tid < 128 && rinfo[tid].x >= 0) {  // F_Theta of this row: c between a and b
+      const int ca = rinfo[tid].y & 0xff, cba = rinfo[tid].y >> 8;
+      unsigned long long kk = 0;
+      for (int ci = 0; ci < nc; ++ci)
+        if (pair_c(clist[ci], ncap) <= ca && pair_cb(clist[ci], ncap) <= cba) kk += cpre[ci + 1] - cpre[ci];
+      flops += 8ull * kk * (unsigned long long)nbt;
+    }
+    auto prep = [&](int k0) -> bool {
+      if (tid < 32) {
+        const int k = k0 + tid;
+        int4 ki = make_int4(-1, 0, 0, 0);
+        if (k < K) {
+          const int ci = find_block(cpre, nc + 1, k);
+          const int cc = clist[ci];
+          ki.x = segC[cc] + (k - cpre[ci]);
+          ki.y = pair_c(cc, ncap);
+          ki.z = pair_cb(cc, ncap);
+        }
+        kinfo[tid] = ki;
+      }
+      return true;
+    };
+    auto lda = [&](int i, int k) -> float2 {
+      const int4 ri = rinfo[i];
+      const int4 ki = kinfo[k & 31];
+      if (ri.x < 0 || ki.x < 0) return make_float2(0.f, 0.f);
+      const int ca = ri.y & 0xff, cba = ri.y >> 8;
+      if (ki.y > ca || ki.z > cba) return make_float2(0.f, 0.f);
+      const float2 w = cmul(fk[ri.z - ki.y], cj(fk[ri.w - ki.z]));
+      const double2 gv = G1[(long long)ri.x * D + ki.x];
+      return cmul(w, make_float2((float)gv.x, (float)gv.y));
+    };
+    auto ldb = [&](int j, int k) -> float2 {
+      const int4 ki = kinfo[k & 31];
+      if (j >= nbt || ki.x < 0) return make_float2(0.f, 0.f);
+      const double2 gv = G2[(long long)ki.x * D + beta0 + j];
+      const double l = lC[ki.x];
+      return make_float2((float)(gv.x * l), (float)(gv.y * l));
+    };
+    auto sto = [&](int i, int j, float re, float im) {
+      if (r0 + i >= R || j >= nbt) return;
+      const int alpha = rinfo[i].x;
+      const float sc = (float)(lA[alpha] * lB[beta0 + j]);
+      Th[sl.f(BF_TOFF, t) + (long long)(r0 + i) * Ccols + col0 + j] = make_float2(re * sc, im * sc);
+    };
+    bool ok;
+    if (nbt <= 32) ok = tc::tile_gemm<MODE, 32>(E, ttsm, K, lda, ldb, sto, prep);
+    else ok = tc::tile_gemm<MODE, THETA_TN>(E, ttsm, K, lda, ldb, sto, prep);
+    if (!ok) break;
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tslot, NCOL);
+  if (st.ctr && flops) {
+    atomicAdd(st.ctr + CTR_THETA, flops);
+    atomicAdd(st.ctr + CTR_FTHETA, flops);
+  }
 }
 
 // ---------------------------------------------------------------- k_gram
@@ -752,7 +970,7 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
 // in FP32: the Gram eigenvectors only seed the one-sided refinement (k_refine),
 // which iterates to the accuracy of the path's own precision from any complete basis.
 template <typename RT>
-__global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr) {
+__global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr, int tc_min) {
   typedef typename Prec<RT>::C CT;
   typedef float2 C;
   const int s = blockIdx.y;
@@ -771,6 +989,7 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
   for (int z = blockIdx.x; z < total; z += gridDim.x) {
     const int t = find_block(gpre, Pc + 1, z);
     const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), gg = sl.f(BF_G, t), side = sl.f(BF_SIDE, t);
+    if (gg >= tc_min) continue;  // on the tensor cores (k_gram_tc); CTA-uniform
     const CT* Th = ThAll + sl.f(BF_TOFF, t);
     C* Gm = GAll + sl.f(BF_GOFF, t);
     const int nt = (gg + TILE - 1) / TILE;
@@ -815,6 +1034,110 @@ __global__ void __launch_bounds__(256) k_gram(SlotWS ws, unsigned long long* ctr
     flops = __reduce_add_sync(0xffffffffu, (unsigned)flops);
     if ((threadIdx.x & 31) == 0 && flops) atomicAdd(ctr + CTR_GRAM, flops);
   }
+}
+
+// ---------------------------------------------------------------- k_gram_tc
+// The Gram matrices of the larger blocks on the tensor cores (tcgen05, see tc.cuh):
+// G = Theta Theta^dag (side 0) or Theta^dag Theta (side 1) in output tiles of 128 x 64
+// complex entries; only tiles holding entries with i <= j are computed, and every
+// such entry is written to G[i][j] and, conjugated, to G[j][i] (the diagonal real).
+// Products in 3xTF32 (FP32-level accuracy), FP32 accumulation.  Blocks with a Gram side below tc_min stay on
+// k_gram.  One TMEM allocation of 256 columns per CTA (at most two CTAs per SM).
+constexpr int GRAM_TN = 64;
+constexpr int GRAM_TC_MIN = 48;
+template <int MODE>
+__host__ __device__ constexpr size_t gram_tc_smem() {
+  return tc::CTile<MODE>::stage_bytes(GRAM_TN) > 80 * 1024 ? tc::CTile<MODE>::stage_bytes(GRAM_TN) : 80 * 1024;
+}
+
+// Output tiles of a block of Gram side gg: 128-row tiles ti, 64-column tiles tj with
+// a column at or right of the tile's first row.
+__device__ __forceinline__ int gram_tc_tiles(int gg) {
+  const int ntr = (gg + 127) / 128, ntc = (gg + GRAM_TN - 1) / GRAM_TN;
+  int n = 0;
+  for (int ti = 0; ti < ntr; ++ti) n += ntc - (128 * ti) / GRAM_TN;
+  return n;
+}
+
+template <typename RT, int MODE>
+__global__ void __launch_bounds__(256) k_gram_tc(SlotWS ws, unsigned long long* ctr, int* err, int tc_min) {
+  typedef typename Prec<RT>::C CT;
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int s = blockIdx.y;
+  Slot sl = get_slot(ws, s);
+  if (sl.scal[SS_STATUS]) return;
+  const int Pc = ws.Pc;
+  int nitems = 0;
+  for (int t = 0; t < Pc; ++t) {
+    const int gg = sl.f(BF_G, t);
+    if (gg >= tc_min) nitems += gram_tc_tiles(gg);
+  }
+  if ((int)blockIdx.x >= nitems) return;  // CTA-uniform, before any TMEM is held
+  const int tid = threadIdx.x;
+  constexpr uint32_t NCOL = tc::CTile<MODE>::tmem_cols(GRAM_TN);
+  if (tid < 32) tc::tmem_alloc(&tslot, NCOL);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  tc::Engine E{tslot, &bar, 0u, err};
+  const CT* ThAll = reinterpret_cast<const CT*>(sl.theta);
+  float2* GAll = reinterpret_cast<float2*>(sl.G);
+  unsigned long long flops = 0;
+  for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
+    int rem = z, t = 0, ti = 0, tj = 0;
+    for (t = 0; t < Pc; ++t) {
+      const int gg = sl.f(BF_G, t);
+      if (gg < tc_min) continue;
+      const int n = gram_tc_tiles(gg);
+      if (rem < n) break;
+      rem -= n;
+    }
+    const int gg = sl.f(BF_G, t), c = sl.f(BF_C, t), r = sl.f(BF_R, t), side = sl.f(BF_SIDE, t);
+    {
+      const int ntc = (gg + GRAM_TN - 1) / GRAM_TN;
+      while (rem >= ntc - (128 * ti) / GRAM_TN) { rem -= ntc - (128 * ti) / GRAM_TN; ++ti; }
+      tj = (128 * ti) / GRAM_TN + rem;
+    }
+    const int i0 = 128 * ti, j0 = GRAM_TN * tj, K = side == 0 ? c : r;
+    const CT* Th = ThAll + sl.f(BF_TOFF, t);
+    float2* Gm = GAll + sl.f(BF_GOFF, t);
+    auto lda = [&](int i, int k) -> float2 {
+      const int gi = i0 + i;
+      if (gi >= gg || k >= K) return make_float2(0.f, 0.f);
+      const float2 v = cvt<float2>(to_d2(side == 0 ? Th[(long long)gi * c + k] : Th[(long long)k * c + gi]));
+      return side == 0 ? v : make_float2(v.x, -v.y);
+    };
+    auto ldb = [&](int j, int k) -> float2 {
+      const int gj = j0 + j;
+      if (gj >= gg || k >= K) return make_float2(0.f, 0.f);
+      const float2 v = cvt<float2>(to_d2(side == 0 ? Th[(long long)gj * c + k] : Th[(long long)k * c + gj]));
+      return side == 0 ? make_float2(v.x, -v.y) : v;
+    };
+    auto st = [&](int i, int j, float re, float im) {
+      const int gi = i0 + i, gj = j0 + j;
+      if (gi >= gg || gj >= gg || gi > gj) return;
+      if (gi == gj) {
+        Gm[(long long)gi * gg + gi] = make_float2(re, 0.f);
+      } else {
+        Gm[(long long)gi * gg + gj] = make_float2(re, im);
+        Gm[(long long)gj * gg + gi] = make_float2(re, -im);
+      }
+    };
+    if (!tc::tile_gemm<MODE, GRAM_TN>(E, gsm, K, lda, ldb, st)) break;
+    if (ctr && tid == 0) {
+      for (int i = i0; i < i0 + 128 && i < gg; ++i) {
+        const int jlo = i > j0 ? i : j0, jhi = (j0 + GRAM_TN < gg ? j0 + GRAM_TN : gg);
+        if (jhi > jlo) flops += 8ull * (unsigned long long)K * (unsigned long long)(jhi - jlo);
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (tid < 32) tc::tmem_dealloc(tslot, NCOL);
+  if (ctr && tid == 0 && flops) atomicAdd(ctr + CTR_GRAM, flops);
 }
 
 // ---------------------------------------------------------------- Jacobi core
@@ -2712,9 +3035,32 @@ int max_svd_clusters() {
   return n;
 }
 
+// The TF32 and BF16 paths contract Theta on the tensor cores (k_theta_tc);
+// GBS_MPO_THETA_SIMT=1 in the environment selects the FP32 SIMT kernel instead (for
+// comparison measurements).
+bool theta_simt() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("GBS_MPO_THETA_SIMT");
+    v = (e && atoi(e) == 1) ? 1 : 0;
+  }
+  return v == 1;
+}
+
+// The tensor-core Gram kernel runs FP32-level (3xTF32) products on every path: the
+// Gram eigenvectors seed the one-sided refinement, whose sweep count grows with the
+// seed's error.
+template <typename R>
+void launch_gram_tc(const MpoDev& s, const SlotWS& ws, int ngates, cudaStream_t st) {
+  int per = (2 * sm_count() + ngates - 1) / ngates;
+  if (per < 1) per = 1;
+  k_gram_tc<R, tc::TC_3XTF32><<<dim3(per, ngates), 256, gram_tc_smem<tc::TC_3XTF32>(), st>>>(ws, s.ctr, s.err,
+                                                                                                GRAM_TC_MIN);
+}
+
 template <typename R>
 void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
-                    cudaStream_t st, cudaEvent_t* ev) {
+                    cudaStream_t st, cudaEvent_t* ev, int mode) {
   const int sms = sm_count();
   int per = (4 * sms + ngates - 1) / ngates;
   if (per < 1) per = 1;
@@ -2726,11 +3072,26 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) record_stage_event(ev[1], st);
   {
     NvtxRange r("gbs_mpo/k_theta");
-    k_theta<R><<<dim3(per, ngates), THETA_WARPS * 32, theta_smem_bytes(s.ncap, sizeof(typename Prec<R>::C)), st>>>(
-        s, ws, d_gates);
+    if (sizeof(R) == 4 && !theta_simt()) {
+      int per_tc = (2 * sms + ngates - 1) / ngates;
+      if (per_tc < 1) per_tc = 1;
+      if (mode == 2)
+        k_theta_tc<tc::TC_BF16><<<dim3(per_tc, ngates), 256, theta_tc_smem<tc::TC_BF16>(s.ncap).total, st>>>(
+            s, ws, d_gates);
+      else
+        k_theta_tc<tc::TC_3XTF32><<<dim3(per_tc, ngates), 256, theta_tc_smem<tc::TC_3XTF32>(s.ncap).total, st>>>(
+            s, ws, d_gates);
+    } else {
+      k_theta<R><<<dim3(per, ngates), THETA_WARPS * 32, theta_smem_bytes(s.ncap, sizeof(typename Prec<R>::C)),
+                   st>>>(s, ws, d_gates);
+    }
   }
   if (ev) record_stage_event(ev[2], st);
-  { NvtxRange r("gbs_mpo/k_gram"); k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr); }
+  {
+    NvtxRange r("gbs_mpo/k_gram");
+    k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr, GRAM_TC_MIN);
+    launch_gram_tc<R>(s, ws, ngates, st);
+  }
   if (ev) record_stage_event(ev[3], st);
   const int svd_ctas = svd_grid<R>(nblk);
   const SvdLayout SL = svd_layout<R>(ws.D, SVD_SMEM);
@@ -2771,6 +3132,19 @@ cudaError_t gate_module_init() {
                              (int)theta_smem_bytes(MPO_NCAP_MAX, sizeof(float2)));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_svd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SVD_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_theta_tc<tc::TC_3XTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)theta_tc_smem<tc::TC_3XTF32>(MPO_NCAP_MAX).total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_theta_tc<tc::TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)theta_tc_smem<tc::TC_BF16>(MPO_NCAP_MAX).total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gram_tc<double, tc::TC_3XTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gram_tc_smem<tc::TC_3XTF32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gram_tc<float, tc::TC_3XTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gram_tc_smem<tc::TC_3XTF32>());
+
   if (e != cudaSuccess) return e;
   g_svd_clusters[0] = max_svd_clusters<double>();
   g_svd_clusters[1] = max_svd_clusters<float>();
@@ -2816,9 +3190,9 @@ int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32) 
 // record nodes of the graph and time every replay.
 void launch_layer(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int ngates, double* d_disc,
                   int prec, cudaStream_t st, int* nlaunch, cudaEvent_t* ev) {
-  if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev);
-  else launch_layer_t<float>(s, ws, d_gates, ngates, d_disc, st, ev);
-  if (nlaunch) *nlaunch += 7;
+  if (prec == 0) launch_layer_t<double>(s, ws, d_gates, ngates, d_disc, st, ev, 0);
+  else launch_layer_t<float>(s, ws, d_gates, ngates, d_disc, st, ev, prec == 2 ? 2 : 1);
+  if (nlaunch) *nlaunch += 8;
 }
 
 void launch_phases(const MpoDev& s, const double* d_phase, cudaStream_t st) {

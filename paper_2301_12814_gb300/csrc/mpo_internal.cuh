@@ -66,7 +66,9 @@ struct MpoDev {
 // algorithmic work counters (real flops of the executed form)
 enum { CTR_THETA = 0, CTR_GRAM, CTR_EIG, CTR_RESPLIT, CTR_SWEEPS, CTR_EIGBLK, CTR_REFINE, CTR_RSWEEPS,
        CTR_NBIG, CTR_CYC_BIG, CTR_CYC_SMALL, CTR_CYC_SEED, CTR_CYC_NS, CTR_CYC_POLISH, CTR_NWARP,
-       CTR_CYC_WARP, CTR_N };
+       CTR_CYC_WARP,
+       CTR_FTHETA,  // F_Theta: real flops of the one-stage Eq. `theta` over the canonical blocks
+       CTR_N };
 
 struct GateDesc {
   int inst, j, out, pad;

@@ -37,7 +37,7 @@ EXPORTS = [
     "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
     "mpo_asymptotic_ee", "mpo_asymptotic_ee_device", "mpo_checkpoint_bytes", "mpo_save", "mpo_load",
-    "mpo_set_allocator",
+    "mpo_set_allocator", "mpo_measure_peaks",
 ]
 ASYM_NMAX = 23  # MPO_ASYM_NMAX
 
@@ -100,6 +100,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_destroy": (None, [_p]),
         "mpo_status_string": (ctypes.c_char_p, [_i]),
         "mpo_observables_static": (_i, [_i, _i, _i, _p, _p, _p, _p, _p, _p, _p]),
+        "mpo_measure_peaks": (_i, [_dp, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -151,6 +152,16 @@ def _ip_of(a: Optional[np.ndarray]):
 def _check(st: int, where: str) -> None:
     if st != 0:
         raise MPOError(st, where)
+
+
+def measure_peaks() -> dict:
+    """Measured peaks of the current GPU in TFLOP/s (mpo_measure_peaks): FP64 and FP32
+    FMA chains, TF32 and BF16 tcgen05 MMA on shared-memory operands."""
+    t = np.zeros(4)
+    ms = np.zeros(4)
+    _check(_lib().mpo_measure_peaks(_d(t), _d(ms)), "mpo_measure_peaks")
+    return {"fp64": float(t[0]), "fp32": float(t[1]), "tf32": float(t[2]), "bf16": float(t[3]),
+            "ms": [float(x) for x in ms]}
 
 
 def svd_cluster_shape() -> dict:
@@ -217,7 +228,7 @@ class Plan:
     def profile(self, with_jacobi: bool = False):
         """One instrumented replay: {stage: (ms, launches, flops)} (and, if asked,
         {blocks, two-sided sweeps, one-sided sweeps})."""
-        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(13)
+        ms = np.zeros(8); nl = np.zeros(8, dtype=np.int32); fl = np.zeros(8); jb = np.zeros(14)
         _check(_lib().mpo_plan_profile(self._h, _d(ms), _ip_of(nl), _d(fl), _d(jb)), "mpo_plan_profile")
         out = {s: (float(ms[i]), int(nl[i]), float(fl[i])) for i, s in enumerate(self.STAGES)}
         if with_jacobi:
@@ -226,7 +237,7 @@ class Plan:
                          "cluster_cycles": float(jb[6]), "cta_cycles": float(jb[7]),
                          "cluster_seed_cycles": float(jb[8]), "cluster_ns_cycles": float(jb[9]),
                          "cluster_polish_cycles": float(jb[10]), "warp_blocks": int(jb[11]),
-                         "warp_cycles": float(jb[12])}
+                         "warp_cycles": float(jb[12]), "theta_F_flops": float(jb[13])}
         return out
 
     def stage_times(self) -> dict:
