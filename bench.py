@@ -41,6 +41,11 @@ ORACLE_SAMPLE_GATES = {"exact_M4_d4": 6, "M16_d6_chi64": 120, "M32_d8_chi256": 1
                        "batched_64x_M16_d6": 60, "M48_d8_chi512": 24}
 # tensor-pipe passes per real product of the contraction kernel, by path
 MMA_PASSES = {"mixed_tf32": 3, "mixed_bf16": 1}
+# DRAM bytes of one launch of the dominant kernel, from an ncu capture of the same
+# kernel code on the same workload (dram__bytes_read.sum + dram__bytes_write.sum);
+# to be retaken whenever the kernel changes
+TRAFFIC = {("M48_d8_chi512", "fp64", "k_svd"):
+           (86.2e6, "profiles/k_svd_M48_d8_chi512_fp64.md: one mid-mesh launch (layer 7), read + write")}
 
 
 def measured_peaks() -> dict:
@@ -146,12 +151,17 @@ def oracle_sample(name: str, n_gates: int, repeats: int = 1, threads: int = 1) -
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def workload_arrays(wl, rank: int):
-    """(instances, meshes) for this rank; batched workloads shift their seeds by rank."""
+def workload_arrays(wl, rank: int, gates: int = 0):
+    """(instances, meshes) for this rank; batched workloads shift their seeds by rank.
+    gates > 0 keeps each mesh's first `gates` gates (and drops its phase screen): a
+    prefix of the workload, the small case for profiler captures."""
     import gbs_workloads as w
     if wl.batch > 1 and rank > 0:
         wl = w.batched_instances(n=wl.batch, first_seed=100 + rank * wl.batch)
     meshes = [wl.mesh(i) for i in range(wl.batch)]
+    if gates > 0:
+        meshes = [w.Mesh(m.M, m.k[:gates], m.theta[:gates], m.phi[:gates], np.zeros(m.M))
+                  if gates < m.n_gates else m for m in meshes]
     return wl, meshes
 
 
@@ -201,7 +211,7 @@ def observable_errors(a, b) -> dict:
             "eps_rel": float(np.max(np.abs(d_a - d_b)) / max(float(np.max(np.abs(d_b))), 1e-300))}
 
 
-def compare_precision(args, wl, n_gates, k, th, ph, fp, obs, stream, other, peaks):
+def compare_precision(args, wl, n_gates, k, th, ph, fp, obs, stream, other, peaks, tuning=None):
     """The same workload on another path: its updates/s (graph replays timed with
     CUDA events, a few steps), its per-stage device times, the observable errors of
     the mixed run against the FP64 run, and the tensor-pipe roofline of its
@@ -209,6 +219,9 @@ def compare_precision(args, wl, n_gates, k, th, ph, fp, obs, stream, other, peak
     import torch
     import paper_2301_12814_gb300 as lib
     G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=other, stream=stream)
+    if tuning:
+        G.set_tuning(**tuning)
+    choices = G.get_tuning()
     plan = G.plan_mesh(n_gates, k, th, ph, fp)
     G.reset(); plan.run()
     steps = max(1, min(args.steps, 5))
@@ -228,24 +241,33 @@ def compare_precision(args, wl, n_gates, k, th, ph, fp, obs, stream, other, peak
     G.reset()
     prof, jac = plan.profile(with_jacobi=True)
     G.close()
-    out = {"precision": other, "value": int(sum(n_gates)) * steps / (ms / 1e3), "unit": "updates/s",
-           "steps": steps, "stages_ms": {s_: round(v, 4) for s_, v in live.items()}}
+    out = {"precision": other, "tuning": choices, "value": int(sum(n_gates)) * steps / (ms / 1e3),
+           "unit": "updates/s", "steps": steps, "stages_ms": {s_: round(v, 4) for s_, v in live.items()}}
     if other != "fp64":
         out["mixed_vs_fp64"] = observable_errors((tr, n1, n2, S, disc), obs)
         fth = jac["theta_F_flops"]
         t_ms = live["theta"]
-        peak = peaks.get("tf32" if other == "mixed_tf32" else "bf16")
-        ach = fth / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
-        passes = MMA_PASSES.get(other, 1)
-        out["contraction_roofline"] = {
-            "kernel": "k_theta_tc", "bound": "tensor", "unit": "TFLOP/s",
-            "algorithmic_flops_per_step": fth, "achieved": ach, "peak": peak,
-            "frac": ach / peak if peak else None,
-            "tensor_pipe_frac": passes * ach / peak if peak else None,
-            "mma_passes": passes,
-            "peak_source": f"{'TF32' if other == 'mixed_tf32' else 'BF16'} tcgen05 peak measured in this run",
-            "note": "frac = F_Theta / stage time / peak; tensor_pipe_frac counts the MMA passes of the split "
-                    "(3xTF32: 3 products per real product), not the padding of partial tiles"}
+        tc_form = choices["theta_form"] == 2 or (choices["theta_form"] == 0 and other == "mixed_bf16")
+        if tc_form:
+            peak = peaks.get("tf32" if other == "mixed_tf32" else "bf16")
+            ach = fth / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+            passes = MMA_PASSES.get(other, 1)
+            out["contraction_roofline"] = {
+                "kernel": "k_theta_tc", "bound": "tensor", "unit": "TFLOP/s",
+                "algorithmic_flops_per_step": fth, "achieved": ach, "peak": peak,
+                "frac": ach / peak if peak else None,
+                "tensor_pipe_frac": passes * ach / peak if peak else None,
+                "mma_passes": passes,
+                "peak_source": f"{'TF32' if other == 'mixed_tf32' else 'BF16'} tcgen05 peak measured in this run",
+                "note": "frac = F_Theta / stage time / peak; tensor_pipe_frac counts the MMA passes of the "
+                        "split (3xTF32: 3 products per real product), not the padding of partial tiles"}
+        else:
+            fl = prof["theta"][2]  # the executed two-stage form's flops
+            ach = fl / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+            out["contraction_roofline"] = {
+                "kernel": "k_theta", "bound": "alu", "unit": "TFLOP/s", "executed_flops_per_step": fl,
+                "F_theta_flops_per_step": fth, "achieved": ach, "peak": peaks["fp32"],
+                "frac": ach / peaks["fp32"], "peak_source": "FP32 FMA-chain peak measured in this run"}
         out["jacobi"] = {"cluster_blocks": jac["cluster_blocks"],
                          "cluster_ms_per_block": jac["cluster_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6,
                          "cluster_ms_split": {k_: jac[f"cluster_{k_}_cycles"] / max(1, jac["cluster_blocks"]) / 2.07e6
@@ -266,7 +288,7 @@ def run_native(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     wl0 = w.workload(args.workload)
-    wl, meshes = workload_arrays(wl0, rank)
+    wl, meshes = workload_arrays(wl0, rank, args.gates)
     prec = args.precision or wl.precision
     if prec not in lib.mpo.PRECISIONS:
         prec = "fp64"
@@ -279,6 +301,14 @@ def run_native(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     peaks = measured_peaks()
     G = lib.MPO(wl.M, wl.d, wl.r, wl.eta, chi_max=wl.chis, batch=wl.batch, precision=prec, stream=stream)
+    tuning = {"autotuned": False, "choices": G.get_tuning()}
+    if args.autotune:
+        from paper_2301_12814_gb300 import autotune as at
+        res = at.autotune(G, n_gates, k, th, ph, fp, precision=prec)
+        tuning = {"autotuned": True, "choices": res["best"], "best_ms_per_mesh": res["best_ms"],
+                  "default_ms_per_mesh": res["default_ms"], "candidates": len(res["table"]),
+                  "fastest": [(round(ms_, 3), c_) for ms_, c_ in res["table"][:4]],
+                  "method": "grid over the launch choices; stage device times of plan replays, best of 2"}
     plan = G.plan_mesh(n_gates, k, th, ph, fp)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
@@ -360,7 +390,10 @@ def run_native(args, ws, rank, local):
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": ("FP64" if fp64_stage else "FP32") + " FMA-chain peak measured in this run "
                                "(mpo_measure_peaks)",
-                "traffic": None, "flops_per_launch": fl_s / max(1, nl_s),
+                "traffic": TRAFFIC.get((args.workload, prec, f"k_{stage}"), (None,))[0] if not args.gates else None,
+                "traffic_source": TRAFFIC.get((args.workload, prec, f"k_{stage}"), (None, None))[1]
+                if not args.gates else None,
+                "flops_per_launch": fl_s / max(1, nl_s),
                 "avg_launch_ms": ms_s / max(1, nl_s), "launches_per_step": nl_s,
                 "timing": "CUDA event record nodes inside the replayed graph, timed steps only"}
     if fl32 > 0:
@@ -370,9 +403,12 @@ def run_native(args, ws, rank, local):
         roofline["two_pipe_frac"] = (fl_s / (peaks["fp64"] * 1e12) + fl32 / (peaks["fp32"] * 1e12)) / (ms_s / 1e3)
     compare = None
     if not args.no_compare:
-        others = ["mixed_tf32", "mixed_bf16"] if prec == "fp64" else ["fp64"]
-        compare = [compare_precision(args, wl, n_gates, k, th, ph, fp, (tr, n1, n2, S, disc), stream, o, peaks)
-                   for o in others]
+        # the mixed paths with their default launch choices, and the TF32 path with its
+        # contraction on the tensor cores (3xTF32) for the tensor-core roofline
+        others = ([("mixed_tf32", None), ("mixed_tf32", {"theta_form": 2}), ("mixed_bf16", None)]
+                  if prec == "fp64" else [("fp64", None)])
+        compare = [compare_precision(args, wl, n_gates, k, th, ph, fp, (tr, n1, n2, S, disc), stream, o, peaks, t)
+                   for o, t in others]
     # CPU oracle on a bounded sample (host cores, single BLAS thread)
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -398,6 +434,8 @@ def run_native(args, ws, rank, local):
         "data": "synthetic",
         "config": {"workload": args.workload, "M": wl.M, "d": wl.d, "chi": wl.chi, "instances": wl.batch,
                    "gates_per_step": units, "precision": prec,
+                   "mesh_prefix_gates": args.gates or None,
+                   "tuning": tuning,
                    "r": float(wl.r[0, 0]), "eta": float(wl.eta[0, 0]), "seeds": wl.seeds[:4],
                    "l2": "flushed: 512 MiB write before each timed step (untimed)",
                    "svd_cluster": lib.mpo.svd_cluster_shape(),
@@ -603,6 +641,10 @@ def main():
     ap.add_argument("--precision", default="fp64",
                     help="path timed as `value` (fp64, mixed_tf32, mixed_bf16); the others go to `compare`")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the handle's launch choices by timing candidates first (recorded in config)")
+    ap.add_argument("--gates", type=int, default=0,
+                    help="run only each mesh's first GATES gates (a prefix, for profiler captures)")
     ap.add_argument("--no-compare", action="store_true", help="skip the run on the other precision")
     args = ap.parse_args()
     if args.warmup < 3:

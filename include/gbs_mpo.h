@@ -324,6 +324,37 @@ mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const
                                   const int* segoff, const double* lam, const void* gam,
                                   double* out, void* cuda_stream);
 
+/* Launch choices of one handle (no counterpart in the paper: tuning knobs of this
+ * implementation, for the autotuner in paper_2301_12814_gb300/autotune.py).  They
+ * change how the work is split over the GPU, never what is computed: every choice
+ * gives the same method; the FP64 path stays within its parity bar and the mixed paths
+ * within their stated bounds (rounding differs between routes).
+ *   theta_form         0 = the path's default (FP64 and TF32: SIMT two-stage; BF16:
+ *                      the tensor-core one-stage contraction in BF16), 1 = SIMT
+ *                      two-stage, 2 = tensor-core one-stage (3xTF32 on the TF32 path,
+ *                      BF16 on the BF16 path; ignored on the FP64 path)
+ *   gram_tc_min        Gram side from which Gram matrices run on the tensor cores
+ *                      (0 = 48); smaller blocks use the SIMT kernel
+ *   svd_cluster_size   CTAs per thread-block cluster of the SVD kernel: 0 = the process
+ *                      default (4, or GBS_MPO_SVD_CLUSTER_SIZE), 1 = no clusters, 2, 4, 8
+ *   svd_cluster_min_n  > 0: every block with a Gram side >= this goes to a cluster;
+ *                      0 = the load rule (a block goes to a cluster when it would hold
+ *                      one SM longer than the layer's average SM); < 0 = no block does
+ *   svd_cluster_seed_max  cluster blocks with a Gram side <= this take the single-CTA
+ *                      Gram seed; -1 = the path's default (FP64 0, FP32 64)
+ * mpo_set_tuning applies to layers issued afterwards: mpo_apply_bs, mpo_sweep_mesh,
+ * mpo_plan_mesh (a plan keeps the choices it was captured with).  MPO_ERR_ARG for
+ * values outside these ranges.  mpo_get_tuning returns the handle's current values. */
+typedef struct {
+  int theta_form;
+  int gram_tc_min;
+  int svd_cluster_size;
+  int svd_cluster_min_n;
+  int svd_cluster_seed_max;
+} mpo_tuning;
+mpo_status mpo_set_tuning(mpo_handle h, const mpo_tuning* t);
+mpo_status mpo_get_tuning(mpo_handle h, mpo_tuning* t);
+
 /* Measured arithmetic peaks of the current GPU, for roofline denominators (a
  * measurement utility; the paper has no counterpart).  tflops[4] (host) receives, in
  * TFLOP/s: FP64 FMA, FP32 FMA (8 independent FMA chains per thread, 8 CTAs of 256

@@ -65,6 +65,7 @@ struct mpo_ctx {
   size_t pin_bytes = 0;
   std::vector<mpo_plan> plans;  // live plans; mpo_destroy destroys them first
   int poisoned = 0;
+  mpo_tuning tun{0, 0, 0, 0, -1};  // launch choices (mpo_set_tuning); defaults
 };
 
 struct mpo_plan_s {
@@ -182,6 +183,24 @@ mpo_status poll_error(mpo_handle h) {
   return MPO_OK;
 }
 
+// The handle's launch choices in the workspace descriptor.  Cluster routing: the load
+// rule, GBS_MPO_SVD_CLUSTER_MIN_N, or the handle's threshold (negative: no block goes
+// to a cluster).  Cluster blocks on the FP64 path all run the FP32 one-sided cluster
+// phase: its seed keeps the small singular values (a Gram seed squares their
+// conditioning), so the critical blocks' FP64 polish needs 2 sweeps instead of 3 to 4
+// (16 modes, chi = 64: 6543 -> 8218 updates/s).  On the FP32 path the single-CTA Gram
+// seed stays for Gram sides up to 64.  GBS_MPO_SVD_CLUSTER_SEED_MAX or the handle's
+// value overrides both.
+void apply_tuning(const mpo_ctx* h, SlotWS& w) {
+  const mpo_tuning& t = h->tun;
+  w.big_min = t.svd_cluster_min_n > 0 ? t.svd_cluster_min_n : t.svd_cluster_min_n < 0 ? 0x3fffffff : svd_big_min();
+  const int sm = t.svd_cluster_seed_max >= 0 ? t.svd_cluster_seed_max : svd_cluster_seed_max();
+  w.cl_seed_max = sm >= 0 ? sm : (h->prec == MPO_FP64 ? 0 : 64);
+  w.theta_form = t.theta_form;
+  w.gram_tc_min = t.gram_tc_min;
+  w.cl_size = t.svd_cluster_size;
+}
+
 mpo_status ensure_slots(mpo_handle h, int need) {
   if (need <= h->nslots) return MPO_OK;
   if (h->ws_buf) {
@@ -192,16 +211,7 @@ mpo_status ensure_slots(mpo_handle h, int need) {
   }
   SlotWS w{};
   w.Pc = h->Pc; w.D = h->D; w.P = h->P;
-  w.big_min = svd_big_min();
-  // Cluster blocks on the FP64 path all run the FP32 one-sided cluster phase: its seed
-  // keeps the small singular values (a Gram seed squares their conditioning), so the
-  // critical blocks' FP64 polish needs 2 sweeps instead of 3 to 4 (16 modes, chi = 64:
-  // 6543 -> 8218 updates/s).  On the FP32 path the single-CTA Gram seed stays for Gram
-  // sides up to 64.  GBS_MPO_SVD_CLUSTER_SEED_MAX overrides both.
-  {
-    const int sm = svd_cluster_seed_max();
-    w.cl_seed_max = sm >= 0 ? sm : (h->prec == MPO_FP64 ? 0 : 64);
-  }
+  apply_tuning(h, w);
   const long long D = h->D;
   w.capRC = (long long)h->Pc * D;
   w.capCand = (long long)h->Pc * D;
@@ -583,6 +593,23 @@ mpo_status mpo_plan_run(mpo_plan p) {
   if (p->h->poisoned) return MPO_ERR_POISONED;
   CK(cudaGraphLaunch(p->exec, p->h->stream));
   ++p->runs;
+  return MPO_OK;
+}
+
+mpo_status mpo_set_tuning(mpo_handle h, const mpo_tuning* t) {
+  if (!h || !t) return MPO_ERR_ARG;
+  if (t->theta_form < 0 || t->theta_form > 2 || t->gram_tc_min < 0 || t->svd_cluster_seed_max < -1) return MPO_ERR_ARG;
+  if (t->svd_cluster_size != 0 && t->svd_cluster_size != 1 && t->svd_cluster_size != 2 &&
+      t->svd_cluster_size != 4 && t->svd_cluster_size != 8)
+    return MPO_ERR_ARG;
+  h->tun = *t;
+  apply_tuning(h, h->ws);  // the pools and tables stay; only the launch choices change
+  return MPO_OK;
+}
+
+mpo_status mpo_get_tuning(mpo_handle h, mpo_tuning* t) {
+  if (!h || !t) return MPO_ERR_ARG;
+  *t = h->tun;
   return MPO_OK;
 }
 

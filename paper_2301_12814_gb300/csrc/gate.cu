@@ -41,6 +41,7 @@
 #include <cooperative_groups.h>
 #include <cstdlib>
 
+#include "dd.cuh"
 #include "mpo_internal.cuh"
 #include "tc.cuh"
 
@@ -81,17 +82,28 @@ template <typename R> struct Prec;
 // re-split divides by the neighbouring bonds' lambda.
 template <> struct Prec<double> {
   typedef double2 C;
+  typedef double T;  // type of the thresholds
   static constexpr double stop2 = 1e-12;
   static constexpr double os_rel = 4e-15, os_abs = 1e-30;
   static constexpr double floor = 1e-28;
 };
 template <> struct Prec<float> {
   typedef float2 C;
+  typedef float T;
   static constexpr double stop2 = 1e-10;
   // off-diagonals below ~3 FP32 ulps of the largest diagonal are rounding noise
   static constexpr float tol_rel = 2e-7f, tol_abs = 2e-7f;
   static constexpr float os_rel = 2e-6f, os_abs = 1e-13f;
   static constexpr double floor = 1e-12;
+};
+// The FP64 path's refinement of cluster blocks in double-float arithmetic (dd.cuh):
+// the same thresholds as FP64, vectors stored as complex double-floats.
+template <> struct Prec<dd> {
+  typedef ddc C;
+  typedef double T;
+  static constexpr double stop2 = Prec<double>::stop2;
+  static constexpr double os_abs = Prec<double>::os_abs;
+  static constexpr double floor = Prec<double>::floor;
 };
 
 // ---- element helpers for real (self-mirror) and complex Jacobi ----
@@ -1637,7 +1649,8 @@ __device__ __forceinline__ int basis_col(int k, const int* mpos, bool selfm, int
 template <typename R>
 __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Prec<R>::C* wq,
                                             typename Prec<R>::C* vp, typename Prec<R>::C* vq, int h, int n,
-                                            bool selfm, R tol_abs, R col_floor, int lane, float& r2) {
+                                            bool selfm, typename Prec<R>::T tol_abs,
+                                            typename Prec<R>::T col_floor, int lane, float& r2) {
   typedef typename Prec<R>::C C;
   R al = 0, be = 0;
   C ga = zero_e<C>();
@@ -1670,6 +1683,73 @@ __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Pr
     vq[x] = lin(s, a, c, bs);
   }
   return true;
+}
+
+// ---- double-float helpers of the FP64 refinement (dd.cuh)
+__device__ __forceinline__ dd dd_shfl_xor(dd v, int o) {
+  return dd_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+// sum over the warp, bitwise the same in every lane (dd_add is commutative bit for bit:
+// both TwoSums are exact)
+__device__ __forceinline__ dd dd_warp_sum(dd v) {
+  for (int o = 16; o > 0; o >>= 1) v = dd_add(v, dd_shfl_xor(v, o));
+  return v;
+}
+__device__ __forceinline__ ddc ddc_conv(double2 a) { return ddc_from(a.x, a.y); }
+__device__ __forceinline__ double2 ddc_back(ddc a) { return make_double2(dd_to(a.re), dd_to(a.im)); }
+
+// One-sided rotation of a column pair in double-float: the inner products by
+// compensated accumulation in every lane and a double-float butterfly, the rotation
+// parameters in FP64 from their FP64 roundings (as on the FP64 path: per pair, not
+// per element), the update of W and V in double-float.
+template <>
+__device__ __forceinline__ bool warp_rotate<dd>(ddc* wp, ddc* wq, ddc* vp, ddc* vq, int h, int n, bool selfm,
+                                                double tol_abs, double col_floor, int lane, float& r2) {
+  dd_acc al = dd_acc_zero(), be = dd_acc_zero(), gr = dd_acc_zero(), gi = dd_acc_zero();
+  for (int x = lane; x < h; x += 32) {
+    const ddc a = wp[x], b = wq[x];
+    dd_acc_mac(al, a.re, a.re);
+    dd_acc_mac(al, a.im, a.im);
+    dd_acc_mac(be, b.re, b.re);
+    dd_acc_mac(be, b.im, b.im);
+    dd_acc_mac(gr, a.re, b.re);  // conj(a) b
+    dd_acc_mac(gr, a.im, b.im);
+    dd_acc_mac(gi, a.re, b.im);
+    dd_acc_mac(gi, dd_neg(a.im), b.re);
+  }
+  const double ald = dd_to(dd_warp_sum(dd_acc_value(al)));
+  const double bed = dd_to(dd_warp_sum(dd_acc_value(be)));
+  const double2 ga = make_double2(dd_to(dd_warp_sum(dd_acc_value(gr))), dd_to(dd_warp_sum(dd_acc_value(gi))));
+  r2 = (ald > col_floor && bed > col_floor) ? rel_off2(ald, bed, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y)
+                                            : 0.f;
+  double c, s;
+  double2 e;
+  if (!os_params(ald, bed, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
+  const dd cd = dd_from(c), sd = dd_from(s), msd = dd_neg(sd);
+  const ddc ec = ddc_from(e.x, -e.y);
+  for (int x = lane; x < h; x += 32) {
+    const ddc a = wp[x], bs = ddc_mul(wq[x], ec);
+    wp[x] = ddc_lin(cd, a, msd, bs);
+    wq[x] = ddc_lin(sd, a, cd, bs);
+  }
+  for (int x = lane; x < n; x += 32) {
+    const ddc a = vp[x], bs = ddc_mul(vq[x], ec);
+    vp[x] = ddc_lin(cd, a, msd, bs);
+    vq[x] = ddc_lin(sd, a, cd, bs);
+  }
+  return true;
+}
+
+// Squared norm of a column of length len, in double-float by one warp (every lane
+// gets the FP64 rounding of the same value).
+__device__ __forceinline__ double ddc_col_norm2(const ddc* w, int len, int lane) {
+  dd_acc a = dd_acc_zero();
+  for (int x = lane; x < len; x += 32) {
+    const ddc v = w[x];
+    dd_acc_mac(a, v.re, v.re);
+    dd_acc_mac(a, v.im, v.im);
+  }
+  return dd_to(dd_warp_sum(dd_acc_value(a)));
 }
 
 // Largest column norm^2 of the columns [k0, k1) of W over the whole cluster.
@@ -1705,8 +1785,8 @@ __device__ R cluster_max_norm2(cg::cluster_group& cl, const typename Prec<R>::C*
 // rotated; *rotations accumulates this CTA's applied rotations.
 template <typename R>
 __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, typename Prec<R>::C* gV, int n,
-                              int h, bool selfm, R tol_abs, R col_floor, unsigned char* smem, const SvdLayout& L,
-                              int* hdr, unsigned long long* rotations) {
+                              int h, bool selfm, typename Prec<R>::T tol_abs, typename Prec<R>::T col_floor,
+                              unsigned char* smem, const SvdLayout& L, int* hdr, unsigned long long* rotations) {
   typedef typename Prec<R>::C C;
   const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
@@ -1854,6 +1934,169 @@ __device__ void cluster_rank(cg::cluster_group& cl, const MpoDev& st, const Slot
   }
 }
 
+// ---------------------------------------------------------------- double-float polish
+// The FP64 path's polish of a cluster block, in double-float arithmetic (dd.cuh):
+// the same steps as the polish in the path precision -- two Newton-Schulz steps on V,
+// W = Theta V afresh, one-sided sweeps to the FP64 thresholds, singular values as
+// column norms -- with every vector operation on pairs of FP32 numbers.  Long inner
+// products are summed in chunks of 16 by compensated accumulation and the chunks
+// combined by dd_add, which bounds their error by ~20 u^2 times the magnitude sum.
+
+// sum_{i < len} conj(a[i sa]) b[i sb] (conj_a) or a[i sa] b[i sb], in double-float
+__device__ __forceinline__ ddc ddc_dot(const ddc* a, long long sa, const ddc* b, long long sb, int len,
+                                       bool conj_a) {
+  dd tr = dd_zero(), ti = dd_zero();
+  for (int i0 = 0; i0 < len; i0 += 16) {
+    dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
+    const int i1 = min(len, i0 + 16);
+    for (int i = i0; i < i1; ++i) {
+      const ddc x = a[(long long)i * sa], y = b[(long long)i * sb];
+      const dd xi = conj_a ? dd_neg(x.im) : x.im;
+      dd_acc_mac(ar, x.re, y.re);
+      dd_acc_mac(ar, dd_neg(xi), y.im);
+      dd_acc_mac(ai, x.re, y.im);
+      dd_acc_mac(ai, xi, y.re);
+    }
+    tr = dd_add(tr, dd_acc_value(ar));
+    ti = dd_add(ti, dd_acc_value(ai));
+  }
+  return ddc_make(tr, ti);
+}
+
+// Largest column norm^2 of the columns [k0, k1) of W over the cluster (FP64 rounding).
+__device__ double cluster_max_norm2_dd(cg::cluster_group& cl, const ddc* W, int h, int k0, int k1, int* hdr,
+                                       double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  double mx = 0;
+  for (int k = k0 + warp; k < k1; k += nwarp) mx = fmax(mx, ddc_col_norm2(W + (long long)k * h, h, lane));
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0;
+    for (int w2 = 0; w2 < nwarp; ++w2) m = fmax(m, red[w2]);
+    *reinterpret_cast<double*>(hdr + HDR_MAX) = m;
+  }
+  cl.sync();
+  double g = 0;
+  for (unsigned r = 0; r < cl.num_blocks(); ++r)
+    g = fmax(g, *cl.map_shared_rank(reinterpret_cast<double*>(hdr + HDR_MAX), r));
+  cl.sync();  // every CTA has read every partial before any is overwritten
+  return g;
+}
+
+// Polish of block t on the cluster.  On entry V (FP32) is the seed: row-major in Vs
+// (Gram seed) or column-major in V32; Theta is FP64.  On exit gW and gV hold W and V
+// as complex128 (the layout the re-split reads) and the singular values are ranked.
+// Returns the sweeps; *rot counts this CTA's rotations.
+__device__ int polish_dd(cg::cluster_group& cl, const MpoDev& st, const Slot& sl, int t, double2* Th,
+                         double2* gW, double2* gV, const float2* Vs, const float2* V32, bool gram_seed, int n,
+                         int h, int r, int c, int side, bool selfm, int k0, int k1, unsigned char* smem,
+                         const SvdLayout& L, int* hdr, unsigned long long* rot, long long* tc, bool timed) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
+  ddc* Vd = reinterpret_cast<ddc*>(gV);
+  ddc* Wd = reinterpret_cast<ddc*>(gW);
+  ddc* Sd = reinterpret_cast<ddc*>(sl.NS) + sl.f(BF_GOFF, t);
+  ddc* Td = Wd;  // W is formed only after Newton-Schulz
+  ddc* Thd = reinterpret_cast<ddc*>(Th);
+  auto lap = [&](int ctr) {
+    if (timed) {
+      const long long now = clock64();
+      atomicAdd(st.ctr + ctr, (unsigned long long)(now - *tc));
+      *tc = now;
+    }
+  };
+  for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // V, column-major, exact in double-float
+    const int k = k0 + (int)(e / n), i = (int)(e % n);
+    const float2 v = gram_seed ? Vs[(long long)i * n + k] : V32[(long long)k * n + i];
+    Vd[(long long)k * n + i] = ddc_make(dd_make(v.x, 0.f), dd_make(v.y, 0.f));
+  }
+  cluster_exchange(cl);
+  for (int it = 0; it < 2; ++it) {
+    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // S[:, k] = V^dag v_k
+      const int k = k0 + (int)(e / n), a = (int)(e % n);
+      Sd[(long long)k * n + a] = ddc_dot(Vd + (long long)a * n, 1, Vd + (long long)k * n, 1, n, true);
+    }
+    cluster_exchange(cl);
+    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // T[:, k] = V (3 e_k - S[:, k]) / 2
+      const int k = k0 + (int)(e / n), i = (int)(e % n);
+      dd tr = dd_zero(), ti = dd_zero();
+      for (int a0 = 0; a0 < n; a0 += 16) {
+        dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
+        const int a1 = min(n, a0 + 16);
+        for (int a = a0; a < a1; ++a) {
+          const ddc sv = Sd[(long long)k * n + a];
+          // w = 1.5 delta_ak - 0.5 S[a, k]  (halving is exact)
+          dd wr = dd_make(-0.5f * sv.re.hi, -0.5f * sv.re.lo);
+          const dd wi = dd_make(-0.5f * sv.im.hi, -0.5f * sv.im.lo);
+          if (a == k) wr = dd_add(wr, dd_make(1.5f, 0.f));
+          const ddc v = Vd[(long long)a * n + i];
+          dd_acc_mac(ar, v.re, wr);
+          dd_acc_mac(ar, dd_neg(v.im), wi);
+          dd_acc_mac(ai, v.re, wi);
+          dd_acc_mac(ai, v.im, wr);
+        }
+        tr = dd_add(tr, dd_acc_value(ar));
+        ti = dd_add(ti, dd_acc_value(ai));
+      }
+      Td[(long long)k * n + i] = ddc_make(tr, ti);
+    }
+    cluster_exchange(cl);
+    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
+      const long long o = (long long)k0 * n + e;
+      Vd[o] = Td[o];
+    }
+    cluster_exchange(cl);
+  }
+  lap(CTR_CYC_NS);
+  {  // Theta to double-float in place (nothing reads it as FP64 afterwards)
+    const long long tot = (long long)r * c, a0 = tot * kr / K, a1 = tot * (kr + 1) / K;
+    for (long long e = a0 + tid; e < a1; e += nth) Thd[e] = ddc_conv(Th[e]);
+  }
+  cluster_exchange(cl);
+  for (long long e = tid; e < (long long)(k1 - k0) * h; e += nth) {  // W = Theta V or Theta^dag V
+    const int k = k0 + (int)(e / h), x = (int)(e % h);
+    Wd[(long long)k * h + x] = side == 1 ? ddc_dot(Thd + (long long)x * c, 1, Vd + (long long)k * n, 1, n, false)
+                                         : ddc_dot(Thd + x, c, Vd + (long long)k * n, 1, n, true);
+  }
+  cluster_exchange(cl);
+  const double mx = cluster_max_norm2_dd(cl, Wd, h, k0, k1, hdr, reinterpret_cast<double*>(smem + L.nrm));
+  const int sw = cluster_sweeps<dd>(cl, Wd, Vd, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, smem, L,
+                                    hdr, rot);
+  if (sw >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3600 + t);
+  lap(CTR_CYC_POLISH);
+  // singular values: column norms of W, ranked descending (ties by index)
+  double* nrm = reinterpret_cast<double*>(Sd);
+  {
+    const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    for (int k = k0 + warp; k < k1; k += nwarp) {
+      const double a = ddc_col_norm2(Wd + (long long)k * h, h, lane);
+      if (lane == 0) nrm[k] = a;
+    }
+  }
+  cluster_exchange(cl);
+  const int coff = sl.f(BF_COFF, t);
+  const int r0 = (int)((long long)kr * n / K), r1 = (int)((long long)(kr + 1) * n / K);
+  for (int i = r0 + tid; i < r1; i += nth) {
+    const double wi = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite(wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4600 + t);
+    sl.sval[coff + rank] = sqrt(wi);
+    sl.perm[coff + rank] = i;
+  }
+  // back to complex128 for the re-split (each CTA its own columns)
+  for (long long e = tid; e < (long long)(k1 - k0) * h; e += nth) {
+    const long long o = (long long)k0 * h + e;
+    gW[o] = ddc_back(Wd[o]);
+  }
+  for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
+    const long long o = (long long)k0 * n + e;
+    gV[o] = ddc_back(Vd[o]);
+  }
+  return sw;
+}
+
 // One large block on the whole cluster (see the section comment).
 template <typename R>
 __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& sl, const GateDesc& g, int t,
@@ -1928,6 +2171,12 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
   }
   lap(CTR_CYC_SEED);
   int sw64 = 0;
+  if constexpr (sizeof(R) == 8) {
+    // the FP64 path polishes in double-float arithmetic (see polish_dd)
+    sw64 = polish_dd(cl, st, sl, t, reinterpret_cast<double2*>(const_cast<C*>(Th)), reinterpret_cast<double2*>(gW),
+                     reinterpret_cast<double2*>(gV), Vs, V32, gram_seed, n, h, r, c, side, selfm, k0, k1, smem, L,
+                     hdr, &rot64, &tc, timed);
+  } else {
   R* nrm = reinterpret_cast<R*>(reinterpret_cast<C*>(sl.NS) + sl.f(BF_GOFF, t));
   {
     // Polish in the path precision: two Newton-Schulz steps V <- V (3 I - V^dag V) / 2
@@ -1985,6 +2234,7 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
   }
   lap(CTR_CYC_POLISH);
   cluster_rank<R>(cl, st, sl, t, gW, nrm, n, h, k0, k1);
+  }
   if (st.ctr && tid == 0) {
     // the FP32 phase counts as the seed, the polish (Newton-Schulz, W = Theta V and
     // the final sweeps, in the path's precision) as the refinement
@@ -2959,9 +3209,11 @@ int sm_count() {
 
 constexpr size_t SVD_SMEM = 200 * 1024;
 // k_svd cluster shape: K CTAs per cluster and the number of such clusters that fit on
-// the GPU at once (per precision), from cudaOccupancyMaxActiveClusters at start-up;
-// 0 clusters = launch without clusters (every large block then runs on one CTA).
-// CTAs per cluster: 4, or GBS_MPO_SVD_CLUSTER_SIZE (1, 2, 4 or 8) from the environment.
+// the GPU at once (per precision and K = 1, 2, 4, 8), from
+// cudaOccupancyMaxActiveClusters at start-up; 0 clusters = launch without clusters
+// (every large block then runs on one CTA).  The process default is 4 CTAs per
+// cluster, or GBS_MPO_SVD_CLUSTER_SIZE (1, 2, 4 or 8) from the environment; a handle
+// may choose another (mpo_set_tuning).
 // Measured on GB300 (updates/s, K = 2 / 4 / 8): 16 modes FP64 5182 / 6131 / 5701, 32
 // modes chi 256 mixed 1187 / 1730 / 1434, 48 modes chi 512 mixed 291 / 476 / 350,
 // 64 instances mixed 71822 / 69018 / 60310.  36 clusters of 4 fit (144 CTAs).
@@ -2977,15 +3229,20 @@ int svd_cluster_size() {
   }
   return v;
 }
-int g_svd_clusters[2] = {0, 0};
+int g_svd_clusters[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // [precision][log2 K]
+__host__ inline int log2_k(int K) { return K >= 8 ? 3 : K >= 4 ? 2 : K >= 2 ? 1 : 0; }
+// clusters of K that fit for precision R (0: launch without clusters)
+template <typename R>
+int svd_clusters(int K) {
+  return K > 1 ? g_svd_clusters[sizeof(R) == 8 ? 0 : 1][log2_k(K)] : 0;
+}
 
 // CTAs of the k_svd launch for a layer of nblk blocks (a multiple of the cluster size
 // when clusters are available).
 template <typename R>
-int svd_grid(int nblk) {
-  const int ncl = g_svd_clusters[sizeof(R) == 8 ? 0 : 1];
+int svd_grid(int nblk, int K) {
+  const int ncl = svd_clusters<R>(K);
   if (ncl > 0) {
-    const int K = svd_cluster_size();
     int want = (nblk + K - 1) / K;
     if (want < 1) want = 1;
     return (want < ncl ? want : ncl) * K;
@@ -2995,8 +3252,9 @@ int svd_grid(int nblk) {
 }
 
 template <typename R>
-cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int grid, cudaStream_t st) {
-  const int ncl = g_svd_clusters[sizeof(R) == 8 ? 0 : 1];
+cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, int grid, int K,
+                       cudaStream_t st) {
+  const int ncl = svd_clusters<R>(K);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   cfg.blockDim = dim3(256);
@@ -3005,7 +3263,7 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
   cfg.gridDim = dim3(grid);
   if (ncl > 0) {
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = svd_cluster_size();
+    at[0].val.clusterDim.x = K;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
@@ -3015,14 +3273,14 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
 }
 
 template <typename R>
-int max_svd_clusters() {
+int max_svd_clusters(int K) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  cfg.gridDim = dim3(svd_cluster_size() * 64);
+  cfg.gridDim = dim3(K * 64);
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = SVD_SMEM;
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = svd_cluster_size();
+  at[0].val.clusterDim.x = K;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
@@ -3035,27 +3293,24 @@ int max_svd_clusters() {
   return n;
 }
 
-// The TF32 and BF16 paths contract Theta on the tensor cores (k_theta_tc);
-// GBS_MPO_THETA_SIMT=1 in the environment selects the FP32 SIMT kernel instead (for
-// comparison measurements).
-bool theta_simt() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("GBS_MPO_THETA_SIMT");
-    v = (e && atoi(e) == 1) ? 1 : 0;
-  }
-  return v == 1;
-}
+// Contraction form by default (mpo_set_tuning overrides it): the BF16 path contracts
+// Theta on the tensor cores in BF16 (k_theta_tc), the FP64 and TF32 paths with the
+// SIMT two-stage kernel (k_theta).  Measured on GB300: the one-stage tensor-core form
+// on the TF32 path took 205 ms per 48-mode chi = 512 mesh against 85 ms for the FP32
+// two-stage kernel, and made the 64-instance batched mesh 2.7x slower (190 vs 71 ms):
+// its 3.4x larger flop count (F_Theta) and the staging of weighted operands cost more
+// than the tensor pipe saves on blocks of these sizes.  The autotuner picks the form
+// per workload.
 
 // The tensor-core Gram kernel runs FP32-level (3xTF32) products on every path: the
 // Gram eigenvectors seed the one-sided refinement, whose sweep count grows with the
 // seed's error.
 template <typename R>
-void launch_gram_tc(const MpoDev& s, const SlotWS& ws, int ngates, cudaStream_t st) {
+void launch_gram_tc(const MpoDev& s, const SlotWS& ws, int ngates, int gmin, cudaStream_t st) {
   int per = (2 * sm_count() + ngates - 1) / ngates;
   if (per < 1) per = 1;
   k_gram_tc<R, tc::TC_3XTF32><<<dim3(per, ngates), 256, gram_tc_smem<tc::TC_3XTF32>(), st>>>(ws, s.ctr, s.err,
-                                                                                                GRAM_TC_MIN);
+                                                                                                gmin);
 }
 
 template <typename R>
@@ -3072,7 +3327,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) record_stage_event(ev[1], st);
   {
     NvtxRange r("gbs_mpo/k_theta");
-    if (sizeof(R) == 4 && !theta_simt()) {
+    const bool tc_theta = sizeof(R) == 4 && (ws.theta_form == 2 || (ws.theta_form == 0 && mode == 2));
+    if (tc_theta) {
       int per_tc = (2 * sms + ngates - 1) / ngates;
       if (per_tc < 1) per_tc = 1;
       if (mode == 2)
@@ -3089,11 +3345,13 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   if (ev) record_stage_event(ev[2], st);
   {
     NvtxRange r("gbs_mpo/k_gram");
-    k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr, GRAM_TC_MIN);
-    launch_gram_tc<R>(s, ws, ngates, st);
+    const int gmin = ws.gram_tc_min > 0 ? ws.gram_tc_min : GRAM_TC_MIN;
+    k_gram<R><<<dim3(per, ngates), 256, 0, st>>>(ws, s.ctr, gmin);
+    launch_gram_tc<R>(s, ws, ngates, gmin, st);
   }
   if (ev) record_stage_event(ev[3], st);
-  const int svd_ctas = svd_grid<R>(nblk);
+  const int K = ws.cl_size > 0 ? ws.cl_size : svd_cluster_size();
+  const int svd_ctas = svd_grid<R>(nblk, K);
   const SvdLayout SL = svd_layout<R>(ws.D, SVD_SMEM);
   const int seed_max = (int)sqrt((double)(SL.total - SL.data) / (2.0 * sizeof(float2)));
   const int room = sizeof(R) == 4 ? (int)(SL.total - SL.data) : 0;
@@ -3102,7 +3360,7 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
     k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max, room);
   }
   if (ev) record_stage_event(ev[4], st);
-  { NvtxRange r("gbs_mpo/k_svd"); launch_svd<R>(s, ws, d_gates, svd_ctas, st); }
+  { NvtxRange r("gbs_mpo/k_svd"); launch_svd<R>(s, ws, d_gates, svd_ctas, K, st); }
   if (ev) record_stage_event(ev[5], st);
   { NvtxRange r("gbs_mpo/k_select"); k_select<<<ngates, 1024, 0, st>>>(s, ws, d_gates, d_disc, Prec<R>::floor); }
   if (ev) record_stage_event(ev[6], st);
@@ -3146,8 +3404,10 @@ cudaError_t gate_module_init() {
                              (int)gram_tc_smem<tc::TC_3XTF32>());
 
   if (e != cudaSuccess) return e;
-  g_svd_clusters[0] = max_svd_clusters<double>();
-  g_svd_clusters[1] = max_svd_clusters<float>();
+  for (int l = 1; l < 4; ++l) {
+    g_svd_clusters[0][l] = max_svd_clusters<double>(1 << l);
+    g_svd_clusters[1][l] = max_svd_clusters<float>(1 << l);
+  }
   return cudaSuccess;
 }
 
@@ -3179,8 +3439,8 @@ int svd_cluster_seed_max() {
 
 int svd_cluster_info(int* cluster_size, int* clusters_fp64, int* clusters_fp32) {
   if (cluster_size) *cluster_size = svd_cluster_size();
-  if (clusters_fp64) *clusters_fp64 = g_svd_clusters[0];
-  if (clusters_fp32) *clusters_fp32 = g_svd_clusters[1];
+  if (clusters_fp64) *clusters_fp64 = svd_clusters<double>(svd_cluster_size());
+  if (clusters_fp32) *clusters_fp32 = svd_clusters<float>(svd_cluster_size());
   return 0;
 }
 

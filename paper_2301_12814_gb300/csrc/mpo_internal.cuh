@@ -127,6 +127,10 @@ struct SlotWS {
   double2* W;      // [S][capTheta] one-sided Jacobi vectors (Theta V or Theta^dag V), column-major
   int big_min;     // > 0: blocks with a Gram side >= big_min go to a CTA cluster (else the load rule)
   int cl_seed_max; // cluster blocks with a Gram side <= this take the single-CTA Gram seed
+  // launch choices of the handle (mpo_set_tuning), read on the host when a layer is issued
+  int theta_form;  // 0: path default, 1: SIMT two-stage, 2: tensor-core one-stage (FP32 paths)
+  int gram_tc_min; // Gram side from which the Gram runs on the tensor cores (0: default)
+  int cl_size;     // CTAs per k_svd cluster (0: process default)
   double2* NS;     // [S][capGram] Newton-Schulz scratch V^dag V of the FP64 refinement
   double2* VC;     // [S][capGram] refined right/left factors, column-major, path precision
                    // (never aliases the FP32 Gram or seed buffers of other blocks)

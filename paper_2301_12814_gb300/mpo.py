@@ -37,7 +37,7 @@ EXPORTS = [
     "mpo_observables", "mpo_truncated_probability", "mpo_operator_entropy", "mpo_get_bonds", "mpo_bond_capacity",
     "mpo_sync", "mpo_destroy", "mpo_status_string", "mpo_observables_static", "mpo_svd_cluster_shape",
     "mpo_asymptotic_ee", "mpo_asymptotic_ee_device", "mpo_checkpoint_bytes", "mpo_save", "mpo_load",
-    "mpo_set_allocator", "mpo_measure_peaks",
+    "mpo_set_allocator", "mpo_measure_peaks", "mpo_set_tuning", "mpo_get_tuning",
 ]
 ASYM_NMAX = 23  # MPO_ASYM_NMAX
 
@@ -47,6 +47,16 @@ class MPOError(RuntimeError):
         self.status = status
         msg = _lib().mpo_status_string(status).decode() if _LIB is not None else str(status)
         super().__init__(f"{where}: {msg} (status {status})")
+
+
+class Tuning(ctypes.Structure):
+    """Launch choices of a handle (mpo_tuning in include/gbs_mpo.h)."""
+    _fields_ = [("theta_form", ctypes.c_int), ("gram_tc_min", ctypes.c_int), ("svd_cluster_size", ctypes.c_int),
+                ("svd_cluster_min_n", ctypes.c_int), ("svd_cluster_seed_max", ctypes.c_int)]
+    NAMES = ("theta_form", "gram_tc_min", "svd_cluster_size", "svd_cluster_min_n", "svd_cluster_seed_max")
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k in self.NAMES}
 
 
 class _Params(ctypes.Structure):
@@ -101,6 +111,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mpo_status_string": (ctypes.c_char_p, [_i]),
         "mpo_observables_static": (_i, [_i, _i, _i, _p, _p, _p, _p, _p, _p, _p]),
         "mpo_measure_peaks": (_i, [_dp, _dp]),
+        "mpo_set_tuning": (_i, [_p, ctypes.POINTER(Tuning)]),
+        "mpo_get_tuning": (_i, [_p, ctypes.POINTER(Tuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,6 +325,24 @@ class MPO:
         _check(_lib().mpo_sweep_mesh(self._h, _ip_of(n_gates), _ip_of(k), _d(theta), _d(phi),
                                      _d(fp), _d(out)), "mpo_sweep_mesh")
         return out[:int(n_gates.sum())]
+
+    def set_tuning(self, **kw) -> dict:
+        """Change launch choices (mpo_set_tuning): theta_form, gram_tc_min,
+        svd_cluster_size, svd_cluster_min_n, svd_cluster_seed_max; unnamed ones keep
+        their current values.  Plans made afterwards use them.  Returns the new set."""
+        t = Tuning()
+        _check(_lib().mpo_get_tuning(self._h, ctypes.byref(t)), "mpo_get_tuning")
+        for key, v in kw.items():
+            if key not in Tuning.NAMES:
+                raise KeyError(key)
+            setattr(t, key, int(v))
+        _check(_lib().mpo_set_tuning(self._h, ctypes.byref(t)), "mpo_set_tuning")
+        return t.as_dict()
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(_lib().mpo_get_tuning(self._h, ctypes.byref(t)), "mpo_get_tuning")
+        return t.as_dict()
 
     def plan_mesh(self, n_gates, k, theta, phi, final_phase=None) -> Plan:
         n_gates, k, theta, phi, fp = self._mesh_arrays(n_gates, k, theta, phi, final_phase)

@@ -34,7 +34,7 @@ def run(name, ngates, precision):
     chi, _, _ = G.bonds()
     out = {"tr": abs(float(gtr[0]) - tr), "n1": rel(gn1[0], n1), "n2": rel(gn2[0], n2),
            "S": float(np.max(np.abs(S[0] - np.array(P.entropy)))),
-           "disc": float(np.max(np.abs(disc - P.discarded))) / max(float(np.max(P.discarded)), 1e-300),
+           "disc_abs": float(np.max(np.abs(disc - P.discarded))), "disc_max": float(np.max(P.discarded)),
            "chi_equal": list(map(int, chi)) == [len(l) for l in P.lam]}
     # bitwise reproducible under the cluster path too
     G.reset()

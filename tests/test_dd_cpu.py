@@ -1,0 +1,26 @@
+"""Accuracy of the double-float arithmetic (csrc/dd.cuh) that the FP64 path's block
+refinement runs in: tests/c_abi/dd_check.cpp includes the header, compares sums,
+products, complex products and 512-term compensated dot products (32 lanes x 16 terms,
+combined pairwise) with long double on random inputs, some near cancellation, and
+fails if an error exceeds a small multiple of u^2 = 2^-48 (relative to the operands'
+magnitudes).  Built here with the host compiler, FMA contraction off."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+def test_double_float_arithmetic_accuracy(tmp_path):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ is needed to build the check")
+    exe = str(tmp_path / "dd_check")
+    subprocess.run([gxx, "-std=c++17", "-O2", "-ffp-contract=off", "-I",
+                    os.path.join(ROOT, "paper_2301_12814_gb300", "csrc"),
+                    os.path.join(HERE, "c_abi", "dd_check.cpp"), "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout

@@ -15,12 +15,15 @@ oracle and the seeded input generators.
   chi = 512 mesh after 24 and 60 gates (every bond the gates touch reaches 512; the
   largest Theta(m) has a Gram side of several hundred, so the cluster route runs
   with w > 1 column blocks per CTA) and the whole 1128-gate mesh.
-* Mixed path: the per-observable bounds stated for it -- on prefixes 1e-4 relative
+* TF32 path: the per-observable bounds stated for it -- on prefixes 1e-4 relative
   (<n>, <n^2>), 1e-3 absolute (S), 1e-4 absolute (Tr), 1e-2 relative to the largest
   (discarded weight); on whole meshes at chi >= 256, where FP32 rounding can swap two
   nearly equal singular values across the chi cut, 5e-2, 1e-2, 2e-3 and 1e-1.
-  Runs: the same meshes, and four instances of the 64-instance batched workload run
-  together in one handle against the oracle run live on each.
+  Runs: the same meshes with both contraction forms, and four instances of the
+  64-instance batched workload run together in one handle against the oracle run
+  live on each.
+* BF16 path: 1e-1 (<n>), 1.2e-1 (<n^2>), 0.25 bits (S), 4e-2 (Tr), 2e-1 (discarded
+  weight), twice the largest errors measured.
 """
 import json
 import os
@@ -37,6 +40,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 RTOL, ATOL = 1e-10, 1e-12
 MIXED_PREFIX = dict(n=1e-4, n2=1e-4, S=1e-3, tr=1e-4, eps=1e-2)
 MIXED_WHOLE = dict(n=5e-2, n2=5e-2, S=1e-2, tr=2e-3, eps=1e-1)
+# BF16 path (one BF16 pass in the contraction: about three significant digits per
+# Theta entry), twice the largest errors measured on these meshes and the 16-mode one
+BF16 = dict(n=1e-1, n2=1.2e-1, S=2.5e-1, tr=4e-2, eps=2e-1)
 
 
 @pytest.fixture(scope="module")
@@ -144,6 +150,35 @@ def test_M48_chi512_whole_mesh_fp64(lib):
 def test_mixed_vs_oracle(lib, name, n, bounds):
     g = golden(name)
     check_mixed(run_gpu(lib, name, n, "mixed_tf32"), snap(g, n), g["discarded"], bounds)
+
+
+@pytest.mark.parametrize("name,n", [("M32_d8_chi256", 120), ("M32_d8_chi256", 496), ("M48_d8_chi512", 60),
+                                    ("M48_d8_chi512", 1128)])
+def test_bf16_vs_oracle(lib, name, n):
+    """The BF16 path (contraction in BF16 on the tensor cores) at its stated bounds."""
+    g = golden(name)
+    check_mixed(run_gpu(lib, name, n, "mixed_bf16"), snap(g, n), g["discarded"], BF16)
+
+
+@pytest.mark.parametrize("name,n,bounds", [("M32_d8_chi256", 120, MIXED_PREFIX), ("M48_d8_chi512", 60, MIXED_PREFIX),
+                                           ("M48_d8_chi512", 1128, MIXED_WHOLE)])
+def test_tf32_tensor_core_contraction_vs_oracle(lib, name, n, bounds):
+    """The TF32 path with its contraction on the tensor cores (3xTF32), the launch
+    choice the autotuner may take, at the mixed bounds."""
+    g = golden(name)
+    wl = w.workload(name)
+    mesh = wl.mesh(0)
+    G = lib.MPO(wl.M, wl.d, wl.r[0], wl.eta[0], chi_max=wl.chi, precision="mixed_tf32")
+    G.set_tuning(theta_form=2)
+    fp = mesh.final_phase if n == mesh.n_gates else None
+    plan = G.plan_mesh([n], mesh.k[:n], mesh.theta[:n], mesh.phi[:n], fp)
+    plan.run()
+    disc = plan.discarded()
+    tr, n1, n2 = G.observables()
+    S, _, _ = G.operator_entropy()
+    G.close()
+    got = dict(trace=tr[0], n_mean=n1[0], n2_mean=n2[0], entropy=S[0], discarded=np.asarray(disc))
+    check_mixed(got, snap(g, n), g["discarded"], bounds)
 
 
 def test_batched_mixed_instances_vs_oracle(lib):
