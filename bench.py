@@ -44,8 +44,7 @@ MMA_PASSES = {"mixed_tf32": 3, "mixed_bf16": 1}
 # DRAM bytes of one launch of the dominant kernel, from an ncu capture of the same
 # kernel code on the same workload (dram__bytes_read.sum + dram__bytes_write.sum);
 # to be retaken whenever the kernel changes
-TRAFFIC = {("M48_d8_chi512", "fp64", "k_svd"):
-           (86.2e6, "profiles/k_svd_M48_d8_chi512_fp64.md: one mid-mesh launch (layer 7), read + write")}
+TRAFFIC = {}
 
 
 def measured_peaks() -> dict:
@@ -389,7 +388,10 @@ def run_native(args, ws, rank, local):
     roofline = {"bound": "alu", "kernel": f"k_{stage}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": ("FP64" if fp64_stage else "FP32") + " FMA-chain peak measured in this run "
-                               "(mpo_measure_peaks)",
+                               "(mpo_measure_peaks)" + (
+                                   "; the counted flops are the FP64-accurate refinement's (run in double-float "
+                                   "arithmetic on the FP32 pipe), so frac compares with doing that work on the "
+                                   "FP64 pipe" if fp64_stage and stage == "svd" else ""),
                 "traffic": TRAFFIC.get((args.workload, prec, f"k_{stage}"), (None,))[0] if not args.gates else None,
                 "traffic_source": TRAFFIC.get((args.workload, prec, f"k_{stage}"), (None, None))[1]
                 if not args.gates else None,

@@ -2253,6 +2253,226 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
   cluster_exchange(cl);
 }
 
+// ---------------------------------------------------------------- double-float refinement (FP64 path, one CTA)
+// refine_sweeps in double-float arithmetic: per round, one warp per pair forms the
+// inner products (compensated, dd.cuh), one thread per pair the rotation parameters
+// in FP64 from their FP64 roundings, one warp per pair applies the rotation in
+// double-float.  Same thresholds and stopping rule as the FP64 sweeps.
+__device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, double tol_abs, double col_floor,
+                                PairWork<double>* pw, int* flags) {
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  const int np = n + (n & 1), half = np / 2;
+  int sweep = 0;
+  for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    __syncthreads();
+    if (tid == 0) { flags[0] = 0; flags[2] = 0; }
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int c0 = 0; c0 < half; c0 += PAIR_CHUNK) {
+        const int cn = (half - c0) < PAIR_CHUNK ? (half - c0) : PAIR_CHUNK;
+        for (int k = warp; k < cn; k += nwarp) {
+          int p, qq;
+          circle_pair(rnd, c0 + k, np, p, qq);
+          if (qq >= n) { if (lane == 0) pw[k].act = 0; continue; }
+          const ddc* wp = W + (long long)p * h;
+          const ddc* wq = W + (long long)qq * h;
+          dd_acc al = dd_acc_zero(), be = dd_acc_zero(), gr = dd_acc_zero(), gi = dd_acc_zero();
+          for (int x = lane; x < h; x += 32) {
+            const ddc a = wp[x], b = wq[x];
+            dd_acc_mac(al, a.re, a.re);
+            dd_acc_mac(al, a.im, a.im);
+            dd_acc_mac(be, b.re, b.re);
+            dd_acc_mac(be, b.im, b.im);
+            dd_acc_mac(gr, a.re, b.re);
+            dd_acc_mac(gr, a.im, b.im);
+            dd_acc_mac(gi, a.re, b.im);
+            dd_acc_mac(gi, dd_neg(a.im), b.re);
+          }
+          const double ald = dd_to(dd_warp_sum(dd_acc_value(al)));
+          const double bed = dd_to(dd_warp_sum(dd_acc_value(be)));
+          const double gre = dd_to(dd_warp_sum(dd_acc_value(gr)));
+          const double gim = dd_to(dd_warp_sum(dd_acc_value(gi)));
+          if (lane == 0) { pw[k].al = ald; pw[k].be = bed; pw[k].ga = make_double2(gre, gim); pw[k].act = 1; }
+        }
+        __syncthreads();
+        for (int k = tid; k < cn; k += nth) {
+          if (!pw[k].act) continue;
+          const double al = pw[k].al, be = pw[k].be;
+          if (al > col_floor && be > col_floor) {
+            const double2 ga = pw[k].ga;
+            const float r2 = rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y);
+            atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(r2));
+          }
+          double c, s;
+          double2 e;
+          if (os_params(al, be, pw[k].ga, selfm, tol_abs, col_floor, c, s, e)) {
+            pw[k].c = c; pw[k].s = s; pw[k].e = e;
+            flags[0] = 1;
+            atomicAdd(&flags[1], 1);
+          } else {
+            pw[k].act = 0;
+          }
+        }
+        __syncthreads();
+        for (int k = warp; k < cn; k += nwarp) {
+          if (!pw[k].act) continue;
+          int p, qq;
+          circle_pair(rnd, c0 + k, np, p, qq);
+          const dd cd = dd_from(pw[k].c), sd = dd_from(pw[k].s), msd = dd_neg(sd);
+          const ddc ec = ddc_from(pw[k].e.x, -pw[k].e.y);
+          ddc* wp = W + (long long)p * h;
+          ddc* wq = W + (long long)qq * h;
+          for (int x = lane; x < h; x += 32) {
+            const ddc a = wp[x], bs = ddc_mul(wq[x], ec);
+            wp[x] = ddc_lin(cd, a, msd, bs);
+            wq[x] = ddc_lin(sd, a, cd, bs);
+          }
+          ddc* vp = Vc + (long long)p * n;
+          ddc* vq = Vc + (long long)qq * n;
+          for (int x = lane; x < n; x += 32) {
+            const ddc a = vp[x], bs = ddc_mul(vq[x], ec);
+            vp[x] = ddc_lin(cd, a, msd, bs);
+            vq[x] = ddc_lin(sd, a, cd, bs);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (!flags[0]) break;
+    if ((double)__uint_as_float((unsigned)flags[2]) < Prec<dd>::stop2) { ++sweep; break; }
+  }
+  __syncthreads();
+  return sweep;
+}
+
+// The FP64 path's refinement of one block on one CTA, in double-float: the steps of
+// refine_block (Newton-Schulz on the FP32 seed, W = Theta V, one-sided sweeps, column
+// norms) with the vectors as complex double-floats; Theta is converted in place, W
+// and V go back to complex128 for the re-split.
+__device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, unsigned char* smem,
+                                const SvdLayout& L, bool seeded) {
+  const int n = sl.f(BF_G, t);
+  const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
+  const int h = side == 0 ? c : r;
+  const bool selfm = pair_mirror(sl.f(BF_M, t), st.ncap) == sl.f(BF_M, t);
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  int* flags = reinterpret_cast<int*>(smem + L.hdr);
+  double* nrm = reinterpret_cast<double*>(smem + L.nrm);
+  PairWork<double>* pw = reinterpret_cast<PairWork<double>*>(smem + L.pw);
+  const size_t room = L.total - L.data;
+  const bool w_smem = (size_t)h * n * sizeof(ddc) <= room;
+  const bool in_smem = ((size_t)h * n + (size_t)n * n) * sizeof(ddc) <= room;
+  double2* Th = reinterpret_cast<double2*>(sl.theta) + sl.f(BF_TOFF, t);
+  ddc* Thd = reinterpret_cast<ddc*>(Th);
+  const float2* V0 = reinterpret_cast<const float2*>(sl.V) + sl.f(BF_GOFF, t);  // row-major FP32 seed
+  ddc* gW = reinterpret_cast<ddc*>(sl.W) + sl.f(BF_TOFF, t);
+  ddc* gVc = reinterpret_cast<ddc*>(sl.VC) + sl.f(BF_GOFF, t);
+  ddc* W = w_smem ? reinterpret_cast<ddc*>(smem + L.data) : gW;
+  ddc* Vc = in_smem ? W + (size_t)h * n : gVc;
+  if (tid == 0) { flags[0] = 0; flags[1] = 0; }
+  if (!seeded) {
+    int* mpos = reinterpret_cast<int*>(smem + L.mpos);
+    if (selfm) block_mirror_map(st, sl, g, t, mpos, reinterpret_cast<int*>(smem + L.seg));
+    for (int e = tid; e < n * n; e += nth) {
+      const int k = e / n, i = e % n;
+      int idx[2];
+      double2 wt[2];
+      const int ne = basis_col<double2, double>(k, mpos, selfm, idx, wt);
+      double2 v = make_double2(0.0, 0.0);
+      for (int u = 0; u < ne; ++u)
+        if (idx[u] == i) v = wt[u];
+      Vc[e] = ddc_conv(v);
+    }
+  } else {
+    // two Newton-Schulz steps V <- V (3 I - V^dag V) / 2 in global scratch (S in the
+    // NS buffer, the product in the W buffer, free until W is formed)
+    ddc* S = reinterpret_cast<ddc*>(sl.NS) + sl.f(BF_GOFF, t);
+    ddc* T = gW;
+    for (int e = tid; e < n * n; e += nth) {
+      const float2 v = V0[(long long)(e % n) * n + e / n];
+      gVc[e] = ddc_make(dd_make(v.x, 0.f), dd_make(v.y, 0.f));
+    }
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+      for (int e = tid; e < n * n; e += nth) {  // S[:, b] = V^dag v_b
+        const int b = e / n, a = e % n;
+        S[e] = ddc_dot(gVc + (long long)a * n, 1, gVc + (long long)b * n, 1, n, true);
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) {  // T[:, b] = V (3 e_b - S[:, b]) / 2
+        const int b = e / n, i = e % n;
+        dd tr = dd_zero(), ti = dd_zero();
+        for (int a0 = 0; a0 < n; a0 += 16) {
+          dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
+          const int a1 = min(n, a0 + 16);
+          for (int a = a0; a < a1; ++a) {
+            const ddc sv = S[(long long)b * n + a];
+            dd wr = dd_make(-0.5f * sv.re.hi, -0.5f * sv.re.lo);
+            const dd wi = dd_make(-0.5f * sv.im.hi, -0.5f * sv.im.lo);
+            if (a == b) wr = dd_add(wr, dd_make(1.5f, 0.f));
+            const ddc v = gVc[(long long)a * n + i];
+            dd_acc_mac(ar, v.re, wr);
+            dd_acc_mac(ar, dd_neg(v.im), wi);
+            dd_acc_mac(ai, v.re, wi);
+            dd_acc_mac(ai, v.im, wr);
+          }
+          tr = dd_add(tr, dd_acc_value(ar));
+          ti = dd_add(ti, dd_acc_value(ai));
+        }
+        T[e] = ddc_make(tr, ti);
+      }
+      __syncthreads();
+      for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
+      __syncthreads();
+    }
+    if (in_smem)
+      for (int e = tid; e < n * n; e += nth) Vc[e] = gVc[e];
+  }
+  for (long long e = tid; e < (long long)r * c; e += nth) Thd[e] = ddc_conv(Th[e]);  // Theta to double-float
+  __syncthreads();
+  for (int e = tid; e < h * n; e += nth) {  // W = Theta V or Theta^dag V
+    const int k = e / h, x = e % h;
+    W[e] = side == 1 ? ddc_dot(Thd + (long long)x * c, 1, Vc + (long long)k * n, 1, n, false)
+                     : ddc_dot(Thd + x, c, Vc + (long long)k * n, 1, n, true);
+  }
+  __syncthreads();
+  double mx = 0;
+  for (int k = warp; k < n; k += nwarp) mx = fmax(mx, ddc_col_norm2(W + (long long)k * h, h, lane));
+  if (lane == 0) nrm[warp] = mx;
+  __syncthreads();
+  mx = 0;
+  for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
+  __syncthreads();
+  const int sweeps =
+      refine_sweeps_dd(W, Vc, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, pw, flags);
+  if (sweeps >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
+  for (int k = warp; k < n; k += nwarp) {
+    const double a = ddc_col_norm2(W + (long long)k * h, h, lane);
+    if (lane == 0) nrm[k] = a;
+  }
+  __syncthreads();
+  const int coff = sl.f(BF_COFF, t);
+  for (int i = tid; i < n; i += nth) {
+    const double wi = nrm[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (nrm[j] > wi) || (nrm[j] == wi && j < i);
+    if (!isfinite(wi)) dev_set_error(st.err, DEV_ERR_NUMERIC, 4500 + t);
+    sl.sval[coff + rank] = sqrt(wi);
+    sl.perm[coff + rank] = i;
+  }
+  // back to complex128 for the re-split (each element read and rewritten by one thread)
+  double2* gWd = reinterpret_cast<double2*>(gW);
+  double2* gVd = reinterpret_cast<double2*>(gVc);
+  for (int e = tid; e < h * n; e += nth) gWd[e] = ddc_back(W[e]);
+  for (int e = tid; e < n * n; e += nth) gVd[e] = ddc_back(Vc[e]);
+  if (st.ctr && tid == 0) {
+    atomicAdd(st.ctr + CTR_REFINE, (unsigned long long)flags[1] * (48ull * h + 24ull * n) +
+                                       8ull * (unsigned long long)h * n * n);
+    atomicAdd(st.ctr + CTR_RSWEEPS, (unsigned long long)(sweeps + 1));
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- refinement
 // One-sided Jacobi (Hestenes) refinement of each canonical block's SVD.  The Gram
 // eigenvectors V (n x n, FP32 seed) give W = Theta V (side 1, n = cols) or
@@ -2269,6 +2489,10 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
 template <typename R>
 __device__ void refine_block(const MpoDev& st, const Slot& sl, const GateDesc& g, int t, unsigned char* smem,
                              const SvdLayout& L, bool seeded) {
+  if constexpr (sizeof(R) == 8) {  // the FP64 path refines in double-float (refine_block_dd)
+    refine_block_dd(st, sl, g, t, smem, L, seeded);
+    return;
+  }
   typedef typename Prec<R>::C C;
   const int n = sl.f(BF_G, t);
   const int r = sl.f(BF_R, t), c = sl.f(BF_C, t), side = sl.f(BF_SIDE, t);
