@@ -96,20 +96,6 @@ __host__ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
 // c x + s y for real double-floats
 __host__ __device__ __forceinline__ dd dd_lin(dd c, dd x, dd s, dd y) { return dd_add(dd_mul(c, x), dd_mul(s, y)); }
 
-// ---- complex
-__host__ __device__ __forceinline__ ddc ddc_make(dd re, dd im) { ddc r; r.re = re; r.im = im; return r; }
-__host__ __device__ __forceinline__ ddc ddc_zero() { return ddc_make(dd_zero(), dd_zero()); }
-__host__ __device__ __forceinline__ ddc ddc_from(double re, double im) { return ddc_make(dd_from(re), dd_from(im)); }
-__host__ __device__ __forceinline__ ddc ddc_conj(ddc a) { return ddc_make(a.re, dd_neg(a.im)); }
-__host__ __device__ __forceinline__ ddc ddc_mul(ddc a, ddc b) {
-  return ddc_make(dd_sub(dd_mul(a.re, b.re), dd_mul(a.im, b.im)), dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re)));
-}
-__host__ __device__ __forceinline__ ddc ddc_add(ddc a, ddc b) { return ddc_make(dd_add(a.re, b.re), dd_add(a.im, b.im)); }
-// c x + s y with real c, s
-__host__ __device__ __forceinline__ ddc ddc_lin(dd c, ddc x, dd s, ddc y) {
-  return ddc_make(dd_lin(c, x.re, s, y.re), dd_lin(c, x.im, s, y.im));
-}
-
 // ---- compensated accumulation (Dot2): sum = hi + (lo + corr)
 struct dd_acc {
   float hi, lo;  // running TwoSum of the leading parts; lo collects every error term
@@ -131,3 +117,29 @@ __host__ __device__ __forceinline__ dd dd_acc_value(dd_acc a) {
   two_sum(a.hi, a.lo, s, e);
   return dd_make(s, e);
 }
+
+// ---- complex.  Products and linear combinations of two terms go through the
+// compensated accumulator: both products exactly (TwoProd of the high parts plus
+// the cross terms), one TwoSum, the rounding errors summed in FP32, then one
+// renormalisation -- an error of a few u^2 relative to the terms' magnitudes, which is
+// what the Jacobi rotations need, at about 28 FP32 operations per result.
+__host__ __device__ __forceinline__ ddc ddc_make(dd re, dd im) { ddc r; r.re = re; r.im = im; return r; }
+__host__ __device__ __forceinline__ ddc ddc_zero() { return ddc_make(dd_zero(), dd_zero()); }
+__host__ __device__ __forceinline__ ddc ddc_from(double re, double im) { return ddc_make(dd_from(re), dd_from(im)); }
+__host__ __device__ __forceinline__ ddc ddc_conj(ddc a) { return ddc_make(a.re, dd_neg(a.im)); }
+// a b + c d for real double-floats
+__host__ __device__ __forceinline__ dd dd_dot2(dd a, dd b, dd c, dd d) {
+  dd_acc s = dd_acc_zero();
+  dd_acc_mac(s, a, b);
+  dd_acc_mac(s, c, d);
+  return dd_acc_value(s);
+}
+__host__ __device__ __forceinline__ ddc ddc_mul(ddc a, ddc b) {
+  return ddc_make(dd_dot2(a.re, b.re, dd_neg(a.im), b.im), dd_dot2(a.re, b.im, a.im, b.re));
+}
+__host__ __device__ __forceinline__ ddc ddc_add(ddc a, ddc b) { return ddc_make(dd_add(a.re, b.re), dd_add(a.im, b.im)); }
+// c x + s y with real c, s
+__host__ __device__ __forceinline__ ddc ddc_lin(dd c, ddc x, dd s, ddc y) {
+  return ddc_make(dd_dot2(c, x.re, s, y.re), dd_dot2(c, x.im, s, y.im));
+}
+

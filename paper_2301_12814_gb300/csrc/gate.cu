@@ -2013,9 +2013,13 @@ __device__ int polish_dd(cg::cluster_group& cl, const MpoDev& st, const Slot& sl
   }
   cluster_exchange(cl);
   for (int it = 0; it < 2; ++it) {
-    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // S[:, k] = V^dag v_k
+    // S[:, k] = V^dag v_k: S is Hermitian, so the entries a <= k are formed and mirrored
+    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
       const int k = k0 + (int)(e / n), a = (int)(e % n);
-      Sd[(long long)k * n + a] = ddc_dot(Vd + (long long)a * n, 1, Vd + (long long)k * n, 1, n, true);
+      if (a > k) continue;
+      const ddc v = ddc_dot(Vd + (long long)a * n, 1, Vd + (long long)k * n, 1, n, true);
+      Sd[(long long)k * n + a] = v;
+      Sd[(long long)a * n + k] = ddc_conj(v);
     }
     cluster_exchange(cl);
     for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // T[:, k] = V (3 e_k - S[:, k]) / 2
@@ -2394,9 +2398,12 @@ __device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc
     }
     __syncthreads();
     for (int it = 0; it < 2; ++it) {
-      for (int e = tid; e < n * n; e += nth) {  // S[:, b] = V^dag v_b
+      for (int e = tid; e < n * n; e += nth) {  // S[:, b] = V^dag v_b, Hermitian: a <= b formed, mirrored
         const int b = e / n, a = e % n;
-        S[e] = ddc_dot(gVc + (long long)a * n, 1, gVc + (long long)b * n, 1, n, true);
+        if (a > b) continue;
+        const ddc v = ddc_dot(gVc + (long long)a * n, 1, gVc + (long long)b * n, 1, n, true);
+        S[e] = v;
+        S[(long long)a * n + b] = ddc_conj(v);
       }
       __syncthreads();
       for (int e = tid; e < n * n; e += nth) {  // T[:, b] = V (3 e_b - S[:, b]) / 2

@@ -4,7 +4,7 @@
 // Reference values come from long double (64-bit significand on x86-64, 113-bit on
 // AArch64), exact for the products and sums checked here to well below the ~2^-47
 // accuracy of a double-float.  Checked over random inputs spanning 2^-40..2^40, with
-// cancellation: dd_add, dd_mul, the complex product, and the compensated dot product
+// cancellation: dd_add, dd_mul, the complex product, c x + s y, and the compensated dot product
 // over 16-term chains combined pairwise with dd_add (the Jacobi inner products: h rows
 // split over 32 lanes, then a butterfly).  Prints the worst relative errors (to the
 // magnitude sum for dot products) and exits 1 if one exceeds its bound.
@@ -42,6 +42,16 @@ int main() {
                   fabsl(val(x.im) * val(y.re));
     if (sc > 0) w_cmul = std::fmax(w_cmul, (double)((fabsl(val(z.re) - re) + fabsl(val(z.im) - im)) / sc));
   }
+  double w_lin = 0;
+  for (int t = 0; t < 100000; ++t) {  // c x + s y: a Jacobi rotation's update
+    const dd c = rnd_dd(g), sn = rnd_dd(g);
+    const ddc x = ddc_make(rnd_dd(g), rnd_dd(g)), y = ddc_make(rnd_dd(g), rnd_dd(g));
+    const ddc z = ddc_lin(c, x, sn, y);
+    const LD re = val(c) * val(x.re) + val(sn) * val(y.re), im = val(c) * val(x.im) + val(sn) * val(y.im);
+    const LD sc = fabsl(val(c) * val(x.re)) + fabsl(val(sn) * val(y.re)) + fabsl(val(c) * val(x.im)) +
+                  fabsl(val(sn) * val(y.im));
+    if (sc > 0) w_lin = std::fmax(w_lin, (double)((fabsl(val(z.re) - re) + fabsl(val(z.im) - im)) / sc));
+  }
   std::normal_distribution<double> nd(0.0, 1.0);
   for (int t = 0; t < 2000; ++t) {
     // 32 lanes x 16 terms of a unit-scale dot product, lane sums combined pairwise
@@ -62,8 +72,10 @@ int main() {
     w_dot = std::fmax(w_dot, (double)(fabsl(val(part[0]) - exact) / mag));
   }
   const double u = std::ldexp(1.0, -24);
-  std::printf("add %.3e mul %.3e cmul %.3e dot %.3e (units of u^2: %.1f %.1f %.1f %.1f)\n", w_add, w_mul, w_cmul,
-              w_dot, w_add / (u * u), w_mul / (u * u), w_cmul / (u * u), w_dot / (u * u));
-  const bool ok = w_add <= 4 * u * u && w_mul <= 8 * u * u && w_cmul <= 16 * u * u && w_dot <= 64 * u * u;
+  std::printf("add %.3e mul %.3e cmul %.3e lin %.3e dot %.3e (units of u^2: %.1f %.1f %.1f %.1f %.1f)\n", w_add,
+              w_mul, w_cmul, w_lin, w_dot, w_add / (u * u), w_mul / (u * u), w_cmul / (u * u), w_lin / (u * u),
+              w_dot / (u * u));
+  const bool ok = w_add <= 4 * u * u && w_mul <= 8 * u * u && w_cmul <= 16 * u * u && w_lin <= 16 * u * u &&
+                  w_dot <= 64 * u * u;
   return ok ? 0 : 1;
 }
