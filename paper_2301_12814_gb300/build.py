@@ -43,6 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, "mpo_internal.cuh"), os.path.join(CSRC, "tc.cuh"),
+               os.path.join(CSRC, "dd.cuh"),
                os.path.join(ROOT, "include", "gbs_mpo.h")]
     jobs = []
     for src in SOURCES:

@@ -82,6 +82,15 @@ __host__ __device__ __forceinline__ dd dd_add(dd a, dd b) {
   return dd_make(s, e);
 }
 __host__ __device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+// a + f for a double-float a and an FP32 f (one TwoSum on the high parts, the low part
+// folded into the error, one renormalisation)
+__host__ __device__ __forceinline__ dd dd_add_f(dd a, float f) {
+  float s, e;
+  two_sum(a.hi, f, s, e);
+  e = DD_ADD(e, a.lo);
+  fast_two_sum(s, e, s, e);
+  return dd_make(s, e);
+}
 
 __host__ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   const float p = DD_MUL(a.hi, b.hi);

@@ -782,7 +782,7 @@ constexpr int THETA_TN = 64;
 // handle's n_cap).  At least 80 KB, so that at most two CTAs share an SM (two TMEM
 // allocations of 256 columns); up to n_cap = 12 it stays within 113 KB, so that two do.
 struct ThetaTcSmem {
-  size_t fk, seg, bpre, clist, cpre, rinfo, kinfo, misc, total;
+  size_t fk, seg, bpre, clist, cpre, rinfo, kinfo, misc, rlam, clam, total;
 };
 template <int MODE>
 __host__ __device__ inline ThetaTcSmem theta_tc_smem(int ncap) {
@@ -796,7 +796,9 @@ __host__ __device__ inline ThetaTcSmem theta_tc_smem(int ncap) {
   L.rinfo = align16(L.cpre + (size_t)(MPO_P_MAX + 1) * sizeof(int));
   L.kinfo = L.rinfo + 128 * sizeof(int4);
   L.misc = L.kinfo + 32 * sizeof(int4);
-  const size_t used = L.misc + 64;
+  L.rlam = L.misc + 64;                   // lambda_A of the tile's rows (FP32)
+  L.clam = L.rlam + 128 * sizeof(float);  // lambda_B of the item's columns (FP32)
+  const size_t used = L.clam + THETA_TN * sizeof(float);
   L.total = used > 80 * 1024 ? used : 80 * 1024;
   return L;
 }
@@ -826,6 +828,10 @@ __global__ void __launch_bounds__(256) k_theta_tc(MpoDev st, SlotWS ws, const Ga
   int4* rinfo = reinterpret_cast<int4*>(ttsm + L.rinfo);
   int4* kinfo = reinterpret_cast<int4*>(ttsm + L.kinfo);
   int* misc = reinterpret_cast<int*>(ttsm + L.misc);
+  // lambda factors in FP32, formed once per row, column and centre index: an FP64
+  // multiply or conversion per staged element would keep the FP64 pipe busy
+  float* rlam = reinterpret_cast<float*>(ttsm + L.rlam);
+  float* clam = reinterpret_cast<float*>(ttsm + L.clam);
   const long long bA = (long long)g.inst * (M + 1) + g.j, bC = bA + 1, bB = bA + 2;
   for (int p = tid; p <= P; p += blockDim.x) {
     segA[p] = st.segoff[bA * (P + 1) + p];
@@ -915,7 +921,9 @@ __global__ void __launch_bounds__(256) k_theta_tc(MpoDev st, SlotWS ws, const Ga
         ri.w = fock_off(db) + (cba - cbm) * (db + 1) + cba;  // + (-cbar_c)
       }
       rinfo[tid] = ri;
+      rlam[tid] = ri.x >= 0 ? (float)lA[ri.x] : 0.f;
     }
+    if (tid < THETA_TN) clam[tid] = tid < nbt ? (float)lB[beta0 + tid] : 0.f;
     __syncthreads();
     const int nc = misc[0], K = cpre[nc];
     if (st.ctr && tid < 128 && rinfo[tid].x >= 0) {  // F_Theta of this row: c between a and b
@@ -935,6 +943,7 @@ __global__ void __launch_bounds__(256) k_theta_tc(MpoDev st, SlotWS ws, const Ga
           ki.x = segC[cc] + (k - cpre[ci]);
           ki.y = pair_c(cc, ncap);
           ki.z = pair_cb(cc, ncap);
+          ki.w = __float_as_int((float)lC[ki.x]);
         }
         kinfo[tid] = ki;
       }
@@ -954,13 +963,12 @@ __global__ void __launch_bounds__(256) k_theta_tc(MpoDev st, SlotWS ws, const Ga
       const int4 ki = kinfo[k & 31];
       if (j >= nbt || ki.x < 0) return make_float2(0.f, 0.f);
       const double2 gv = G2[(long long)ki.x * D + beta0 + j];
-      const double l = lC[ki.x];
-      return make_float2((float)(gv.x * l), (float)(gv.y * l));
+      const float l = __int_as_float(ki.w);
+      return make_float2((float)gv.x * l, (float)gv.y * l);
     };
     auto sto = [&](int i, int j, float re, float im) {
       if (r0 + i >= R || j >= nbt) return;
-      const int alpha = rinfo[i].x;
-      const float sc = (float)(lA[alpha] * lB[beta0 + j]);
+      const float sc = rlam[i] * clam[j];
       Th[sl.f(BF_TOFF, t) + (long long)(r0 + i) * Ccols + col0 + j] = make_float2(re * sc, im * sc);
     };
     bool ok;
@@ -1698,6 +1706,43 @@ __device__ __forceinline__ dd dd_warp_sum(dd v) {
 __device__ __forceinline__ ddc ddc_conv(double2 a) { return ddc_from(a.x, a.y); }
 __device__ __forceinline__ double2 ddc_back(ddc a) { return make_double2(dd_to(a.re), dd_to(a.im)); }
 
+// Rotation angles below this apply through FP32 corrections (ddc_rotate).
+constexpr double DD_SMALL_ROT = 1e-7;
+
+// Apply the rotation (c, s, e) to the column pair (x, y) in double-float, elements
+// lane, lane + 32, ... < len.  Large angles: x' = c x - s conj(e) y, y' = s x + c conj(e) y
+// (the column-q phase form of the FP64 path).  Angles |s| < DD_SMALL_ROT: the
+// phase-free rotation x' = c x - s conj(e) y, y' = c y + s e x -- the same unitary up
+// to the phase conj(e) on column q, a gauge that W and V share (the product W V^dag,
+// and with it X and Y of the re-split, is unchanged) -- written as x + dx, y + dy with
+// dx = (c - 1) x - s conj(e) y and dy = (c - 1) y + s e x formed in FP32 from the high
+// parts: |dx|, |dy| <= ~1e-7 |x, y|, so the FP32 rounding and the neglected low parts
+// stay near 1e-14 relative, and an element costs a TwoSum per component instead of two
+// double-float products.
+__device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, double c, double s, double2 e) {
+  if (fabs(s) < DD_SMALL_ROT) {
+    const float cm1 = (float)(c - 1.0), sf = (float)s;
+    const float er = (float)e.x, ei = (float)e.y;
+    for (int k = lane; k < len; k += 32) {
+      const ddc a = x[k], b = y[k];
+      const float ceb_r = er * b.re.hi + ei * b.im.hi, ceb_i = er * b.im.hi - ei * b.re.hi;  // conj(e) b
+      const float ea_r = er * a.re.hi - ei * a.im.hi, ea_i = er * a.im.hi + ei * a.re.hi;    // e a
+      const float dxr = cm1 * a.re.hi - sf * ceb_r, dxi = cm1 * a.im.hi - sf * ceb_i;
+      const float dyr = cm1 * b.re.hi + sf * ea_r, dyi = cm1 * b.im.hi + sf * ea_i;
+      x[k] = ddc_make(dd_add_f(a.re, dxr), dd_add_f(a.im, dxi));
+      y[k] = ddc_make(dd_add_f(b.re, dyr), dd_add_f(b.im, dyi));
+    }
+    return;
+  }
+  const dd cd = dd_from(c), sd = dd_from(s), msd = dd_neg(sd);
+  const ddc ec = ddc_from(e.x, -e.y);
+  for (int k = lane; k < len; k += 32) {
+    const ddc a = x[k], bs = ddc_mul(y[k], ec);
+    x[k] = ddc_lin(cd, a, msd, bs);
+    y[k] = ddc_lin(sd, a, cd, bs);
+  }
+}
+
 // One-sided rotation of a column pair in double-float: the inner products by
 // compensated accumulation in every lane and a double-float butterfly, the rotation
 // parameters in FP64 from their FP64 roundings (as on the FP64 path: per pair, not
@@ -1725,18 +1770,8 @@ __device__ __forceinline__ bool warp_rotate<dd>(ddc* wp, ddc* wq, ddc* vp, ddc* 
   double c, s;
   double2 e;
   if (!os_params(ald, bed, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
-  const dd cd = dd_from(c), sd = dd_from(s), msd = dd_neg(sd);
-  const ddc ec = ddc_from(e.x, -e.y);
-  for (int x = lane; x < h; x += 32) {
-    const ddc a = wp[x], bs = ddc_mul(wq[x], ec);
-    wp[x] = ddc_lin(cd, a, msd, bs);
-    wq[x] = ddc_lin(sd, a, cd, bs);
-  }
-  for (int x = lane; x < n; x += 32) {
-    const ddc a = vp[x], bs = ddc_mul(vq[x], ec);
-    vp[x] = ddc_lin(cd, a, msd, bs);
-    vq[x] = ddc_lin(sd, a, cd, bs);
-  }
+  ddc_rotate(wp, wq, h, lane, c, s, e);
+  ddc_rotate(vp, vq, n, lane, c, s, e);
   return true;
 }
 
@@ -2322,22 +2357,8 @@ __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, doubl
           if (!pw[k].act) continue;
           int p, qq;
           circle_pair(rnd, c0 + k, np, p, qq);
-          const dd cd = dd_from(pw[k].c), sd = dd_from(pw[k].s), msd = dd_neg(sd);
-          const ddc ec = ddc_from(pw[k].e.x, -pw[k].e.y);
-          ddc* wp = W + (long long)p * h;
-          ddc* wq = W + (long long)qq * h;
-          for (int x = lane; x < h; x += 32) {
-            const ddc a = wp[x], bs = ddc_mul(wq[x], ec);
-            wp[x] = ddc_lin(cd, a, msd, bs);
-            wq[x] = ddc_lin(sd, a, cd, bs);
-          }
-          ddc* vp = Vc + (long long)p * n;
-          ddc* vq = Vc + (long long)qq * n;
-          for (int x = lane; x < n; x += 32) {
-            const ddc a = vp[x], bs = ddc_mul(vq[x], ec);
-            vp[x] = ddc_lin(cd, a, msd, bs);
-            vq[x] = ddc_lin(sd, a, cd, bs);
-          }
+          ddc_rotate(W + (long long)p * h, W + (long long)qq * h, h, lane, pw[k].c, pw[k].s, pw[k].e);
+          ddc_rotate(Vc + (long long)p * n, Vc + (long long)qq * n, n, lane, pw[k].c, pw[k].s, pw[k].e);
         }
         __syncthreads();
       }
@@ -2659,7 +2680,18 @@ __device__ void refine_block(const MpoDev& st, const Slot& sl, const GateDesc& g
 // rest (a separate phase).  The results go where the CTA path puts them (sval, perm,
 // W, VC).
 constexpr int WARP_SVD_N = 64;
-constexpr int SVD_WARPS = 8;
+constexpr int SVD_WARPS = 8;  // shared-memory slices of the warp-block phase
+// Threads of a k_svd CTA.  One CTA holds an SM (its ~200 KB shared-memory block), so
+// the CTA's warps are the SM's parallelism: the Jacobi rounds give each warp a pair at
+// a time, and with 16 warps a round of b pairs takes half the turns it takes with 8.
+// Measured on GB300 (48 modes, chi = 512): 256 threads 196 updates/s (FP64) and 514
+// (TF32), 512 threads 234 and 692, at 128 registers per thread without spills on
+// the FP64 path.
+#ifndef MPO_SVD_THREADS
+#define MPO_SVD_THREADS 512
+#endif
+constexpr int SVD_THREADS = MPO_SVD_THREADS;
+static_assert(SVD_THREADS % 32 == 0 && SVD_THREADS >= 32 * SVD_WARPS && SVD_THREADS <= 1024, "k_svd CTA size");
 
 // A warp's slice: [header: rotation parameters of up to 32 pairs, the mirror map and
 // the column norms, 1280 B | seed A and V (padded rows), later W (n columns of stride
@@ -3037,7 +3069,7 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
 // is reached by all CTAs of the cluster: the work item is broadcast from the
 // cluster's first CTA and every loop bound inside big_block is cluster-uniform.
 template <typename R>
-__global__ void __launch_bounds__(256, 1) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
+__global__ void __launch_bounds__(SVD_THREADS, 1) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
                                              const int* __restrict__ list, int* counter, int smem_bytes) {
   extern __shared__ __align__(256) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -3488,7 +3520,7 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
   const int ncl = svd_clusters<R>(K);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(SVD_THREADS);
   cfg.dynamicSmemBytes = SVD_SMEM;
   cfg.stream = st;
   cfg.gridDim = dim3(grid);
@@ -3508,7 +3540,7 @@ int max_svd_clusters(int K) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   cfg.gridDim = dim3(K * 64);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(SVD_THREADS);
   cfg.dynamicSmemBytes = SVD_SMEM;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = K;
