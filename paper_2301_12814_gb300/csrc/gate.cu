@@ -59,7 +59,12 @@ constexpr int JACOBI_MAX_SWEEPS = 60;
 // path) and its Jacobi work estimate n^2 (n + h) exceeds the layer's total over the
 // CTAs of k_svd, i.e. it alone would hold one SM longer than the average SM is busy.
 // A throughput-bound layer (many instances) therefore keeps every block on one CTA.
+// Blocks of Gram side >= SVD_CLUSTER_ALWAYS_N go to a cluster in any case: on one CTA
+// such a block costs more SM-time than on a cluster (48 modes, chi = 512: 4.51 against
+// 4.82 s per FP64 mesh, 1.46 against 1.63 s per TF32 mesh with the blocks from 96 up
+// on clusters; the load rule alone put them there from about 110).
 // ws.big_min > 0 replaces the rule by "Gram side >= big_min" (used by the tests).
+constexpr int SVD_CLUSTER_ALWAYS_N = 96;
 template <typename R> struct SvdRoute;
 template <> struct SvdRoute<double> { static constexpr int min_n = 16; };
 template <> struct SvdRoute<float> { static constexpr int min_n = 48; };
@@ -2684,14 +2689,16 @@ constexpr int SVD_WARPS = 8;  // shared-memory slices of the warp-block phase
 // Threads of a k_svd CTA.  One CTA holds an SM (its ~200 KB shared-memory block), so
 // the CTA's warps are the SM's parallelism: the Jacobi rounds give each warp a pair at
 // a time, and with 16 warps a round of b pairs takes half the turns it takes with 8.
-// Measured on GB300 (48 modes, chi = 512): 256 threads 196 updates/s (FP64) and 514
-// (TF32), 512 threads 234 and 692, at 128 registers per thread without spills on
-// the FP64 path.
-#ifndef MPO_SVD_THREADS
-#define MPO_SVD_THREADS 512
-#endif
-constexpr int SVD_THREADS = MPO_SVD_THREADS;
-static_assert(SVD_THREADS % 32 == 0 && SVD_THREADS >= 32 * SVD_WARPS && SVD_THREADS <= 1024, "k_svd CTA size");
+// Measured on GB300 (48 modes, chi = 512, updates/s):
+//   threads        256   512   768   1024
+//   FP64 path      196   234   222   223    (128 registers at 512, no spills)
+//   TF32 path      514   692   771   784
+// The FP64 path's double-float polish needs the registers of 512 threads; the FP32
+// path's Jacobi gains from more warps despite a few spilled registers at 1024.
+template <typename R> struct SvdThreads;
+template <> struct SvdThreads<double> { static constexpr int value = 512; };
+template <> struct SvdThreads<float> { static constexpr int value = 1024; };
+static_assert(SvdThreads<double>::value >= 32 * SVD_WARPS && SvdThreads<float>::value <= 1024, "k_svd CTA size");
 
 // A warp's slice: [header: rotation parameters of up to 32 pairs, the mirror map and
 // the column norms, 1280 B | seed A and V (padded rows), later W (n columns of stride
@@ -2974,7 +2981,8 @@ __device__ void warp_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 __device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int min_n, int seed_max,
                                           unsigned long long total, int ncta) {
   if (ws.big_min > 0) return n >= ws.big_min;
-  return n >= min_n && (n > seed_max || svd_work(n, h) * (unsigned long long)ncta > total);
+  return n >= min_n &&
+         (n > seed_max || n >= SVD_CLUSTER_ALWAYS_N || svd_work(n, h) * (unsigned long long)ncta > total);
 }
 
 // category: 0 cluster, 1 one CTA, 2 one warp in a quarter slice, 3 one warp in an
@@ -3069,7 +3077,7 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
 // is reached by all CTAs of the cluster: the work item is broadcast from the
 // cluster's first CTA and every loop bound inside big_block is cluster-uniform.
 template <typename R>
-__global__ void __launch_bounds__(SVD_THREADS, 1) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
+__global__ void __launch_bounds__(SvdThreads<R>::value, 1) k_svd(MpoDev st, SlotWS ws, const GateDesc* __restrict__ gates,
                                              const int* __restrict__ list, int* counter, int smem_bytes) {
   extern __shared__ __align__(256) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -3520,7 +3528,7 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
   const int ncl = svd_clusters<R>(K);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  cfg.blockDim = dim3(SVD_THREADS);
+  cfg.blockDim = dim3(SvdThreads<R>::value);
   cfg.dynamicSmemBytes = SVD_SMEM;
   cfg.stream = st;
   cfg.gridDim = dim3(grid);
@@ -3540,7 +3548,7 @@ int max_svd_clusters(int K) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   cfg.gridDim = dim3(K * 64);
-  cfg.blockDim = dim3(SVD_THREADS);
+  cfg.blockDim = dim3(SvdThreads<R>::value);
   cfg.dynamicSmemBytes = SVD_SMEM;
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = K;
