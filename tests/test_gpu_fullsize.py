@@ -22,12 +22,13 @@ oracle and the seeded input generators.
   Runs: the same meshes with both contraction forms, and four instances of the
   64-instance batched workload run together in one handle against the oracle run
   live on each.
-* BF16 path: 3e-1 (<n>, <n^2>), 0.3 bits (S), 4e-2 (Tr), 2e-1 (discarded weight).
+* BF16 path: 3e-1 (<n>, <n^2>), 0.3 bits (S), 1e-1 (Tr), 2e-1 (discarded weight).
   A BF16 operand rounds at 2^-9 relative, far above the relative gaps between the
   singular values at the chi cut of these heavily truncated meshes, so which states
-  are kept depends on the rounding of the staged operands: builds that differ only in
-  the FP32 rounding of the lambda factors measured up to 4e-2 and 1.5e-1 on <n>.
-  The bounds are twice the largest error measured over such builds.
+  are kept depends on the rounding of the staged operands and on the SVD's order of
+  operations: builds that differ only there measured up to 1.5e-1 on <n> and 4.0e-2
+  on Tr (the whole 48-mode mesh, where the truncated weight 1 - Tr is 0.54).  The
+  bounds are about twice the largest error measured over such builds.
 """
 import json
 import os
@@ -46,8 +47,8 @@ MIXED_PREFIX = dict(n=1e-4, n2=1e-4, S=1e-3, tr=1e-4, eps=1e-2)
 MIXED_WHOLE = dict(n=5e-2, n2=5e-2, S=1e-2, tr=2e-3, eps=1e-1)
 # BF16 path (one BF16 pass in the contraction: about three significant digits per
 # Theta entry), twice the largest errors measured on these meshes and the 16-mode one
-# over builds that differ only in FP32 rounding order (the swaps at the chi cut)
-BF16 = dict(n=3e-1, n2=3e-1, S=3e-1, tr=4e-2, eps=2e-1)
+# over builds that differ only in rounding order (the swaps at the chi cut)
+BF16 = dict(n=3e-1, n2=3e-1, S=3e-1, tr=1e-1, eps=2e-1)
 
 
 @pytest.fixture(scope="module")
