@@ -60,11 +60,14 @@ constexpr int JACOBI_MAX_SWEEPS = 60;
 // CTAs of k_svd, i.e. it alone would hold one SM longer than the average SM is busy.
 // A throughput-bound layer (many instances) therefore keeps every block on one CTA.
 // Blocks of Gram side >= SVD_CLUSTER_ALWAYS_N go to a cluster in any case: on one CTA
-// such a block costs more SM-time than on a cluster (48 modes, chi = 512: 4.51 against
-// 4.82 s per FP64 mesh, 1.46 against 1.63 s per TF32 mesh with the blocks from 96 up
-// on clusters; the load rule alone put them there from about 110).
+// such a block costs more SM-time than on a cluster.  48 modes, chi = 512, every block
+// from a Gram side n0 up on a cluster (and no other), s per mesh:
+//   n0          64     80     96     112    128    (load rule alone: from about 110)
+//   FP64       4.24   4.46   4.51   5.31   5.72    (4.51)
+//   TF32       1.26   1.31   1.35   1.46   1.57    (1.35)
+// At 32 modes and chi = 256 the load rule already sends the blocks from ~60 up.
 // ws.big_min > 0 replaces the rule by "Gram side >= big_min" (used by the tests).
-constexpr int SVD_CLUSTER_ALWAYS_N = 96;
+constexpr int SVD_CLUSTER_ALWAYS_N = 64;
 template <typename R> struct SvdRoute;
 template <> struct SvdRoute<double> { static constexpr int min_n = 16; };
 template <> struct SvdRoute<float> { static constexpr int min_n = 48; };
@@ -2699,6 +2702,15 @@ template <typename R> struct SvdThreads;
 template <> struct SvdThreads<double> { static constexpr int value = 512; };
 template <> struct SvdThreads<float> { static constexpr int value = 1024; };
 static_assert(SvdThreads<double>::value >= 32 * SVD_WARPS && SvdThreads<float>::value <= 1024, "k_svd CTA size");
+// Threads of a k_svd launch (every code path of the kernel works for any multiple of
+// 32 from 32 * SVD_WARPS up to the bound above).  The FP64 path with bonds of at most
+// 64 has blocks of Gram side <= ~30, whose rounds keep few warps busy while every
+// barrier waits for all of them: 256 threads there (16 modes, chi = 64: 8449 against
+// 7670 updates/s with 512; the FP32 path is faster with 1024 there too).
+template <typename R>
+__host__ inline int svd_threads(int D) {
+  return (sizeof(R) == 8 && D <= 64) ? 256 : SvdThreads<R>::value;
+}
 
 // A warp's slice: [header: rotation parameters of up to 32 pairs, the mirror map and
 // the column norms, 1280 B | seed A and V (padded rows), later W (n columns of stride
@@ -3528,7 +3540,7 @@ cudaError_t launch_svd(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gate
   const int ncl = svd_clusters<R>(K);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
-  cfg.blockDim = dim3(SvdThreads<R>::value);
+  cfg.blockDim = dim3(svd_threads<R>(ws.D));
   cfg.dynamicSmemBytes = SVD_SMEM;
   cfg.stream = st;
   cfg.gridDim = dim3(grid);
