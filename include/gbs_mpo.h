@@ -340,7 +340,8 @@ mpo_status mpo_observables_static(int M, int n_cap, int D, const int* chi, const
  *   svd_cluster_min_n  > 0: every block with a Gram side >= this goes to a cluster;
  *                      0 = the load rule (a block goes to a cluster when it would hold
  *                      one SM longer than the layer's average SM, or when its Gram side
- *                      is at least 64); < 0 = no block does
+ *                      is at least 48 on the FP64 path, 64 on the others); < 0 = no
+ *                      block does
  *   svd_cluster_seed_max  cluster blocks with a Gram side <= this take the single-CTA
  *                      Gram seed; -1 = the path's default (FP64 0, FP32 64)
  * mpo_set_tuning applies to layers issued afterwards: mpo_apply_bs, mpo_sweep_mesh,

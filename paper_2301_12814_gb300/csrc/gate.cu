@@ -41,6 +41,7 @@
 #include <cooperative_groups.h>
 #include <cstdlib>
 
+#include <type_traits>
 #include "dd.cuh"
 #include "mpo_internal.cuh"
 #include "tc.cuh"
@@ -54,23 +55,26 @@ constexpr double TIE_REL = 1e-9;
 constexpr int JACOBI_MAX_SWEEPS = 60;
 // Which blocks are factorised on a whole thread-block cluster (see the large-block
 // section) instead of one CTA: those that would otherwise be the layer's critical
-// path.  A block goes to a cluster when its Gram side is at least SVD_MIN_N (16 on
-// the FP64 path, whose FP64 refinement runs at 1/64 of the FP32 rate, 48 on the FP32
-// path) and its Jacobi work estimate n^2 (n + h) exceeds the layer's total over the
-// CTAs of k_svd, i.e. it alone would hold one SM longer than the average SM is busy.
-// A throughput-bound layer (many instances) therefore keeps every block on one CTA.
-// Blocks of Gram side >= SVD_CLUSTER_ALWAYS_N go to a cluster in any case: on one CTA
-// such a block costs more SM-time than on a cluster.  48 modes, chi = 512, every block
-// from a Gram side n0 up on a cluster (and no other), s per mesh:
-//   n0          64     80     96     112    128    (load rule alone: from about 110)
-//   FP64       4.24   4.46   4.51   5.31   5.72    (4.51)
-//   TF32       1.26   1.31   1.35   1.46   1.57    (1.35)
-// At 32 modes and chi = 256 the load rule already sends the blocks from ~60 up.
+// path, and the large ones.  A block goes to a cluster when its Gram side is at least
+// min_n and either its Jacobi work estimate n^2 (n + h) exceeds the layer's total over
+// the CTAs of k_svd (it alone would hold one SM longer than the average SM is busy),
+// or its Gram side is at least always_n (on one CTA such a block costs more SM-time
+// than on a cluster).  A throughput-bound layer of small blocks (many instances)
+// therefore keeps every block on one CTA.  Measured on GB300, s per mesh with every
+// block from a Gram side n0 up on a cluster and no other (the load rule alone sent
+// blocks there from about 110 at 48 modes and about 60 at 32 modes):
+//   n0                       48     64     80     96     112    128    load rule
+//   48 modes chi 512 FP64   4.23   4.24   4.46   4.51   5.31   5.72   4.51
+//   48 modes chi 512 TF32   1.33   1.26   1.31   1.35   1.46   1.57   1.35
+//   32 modes chi 256 FP64   0.426  0.472                             0.462
+//   32 modes chi 256 TF32   0.210  0.185                             0.197
+// The FP64 path (min_n 16: its refinement is the expensive part, and small critical
+// blocks gain from a cluster, 16 modes chi 64: +26 %) sends every block from 48 up;
+// the FP32 path (CTAs of 1024 threads) keeps blocks below 64 on one CTA.
 // ws.big_min > 0 replaces the rule by "Gram side >= big_min" (used by the tests).
-constexpr int SVD_CLUSTER_ALWAYS_N = 64;
 template <typename R> struct SvdRoute;
-template <> struct SvdRoute<double> { static constexpr int min_n = 16; };
-template <> struct SvdRoute<float> { static constexpr int min_n = 48; };
+template <> struct SvdRoute<double> { static constexpr int min_n = 16, always_n = 48; };
+template <> struct SvdRoute<float> { static constexpr int min_n = 64, always_n = 64; };
 __device__ __forceinline__ unsigned long long svd_work(int n, int h) {
   return (unsigned long long)n * n * (unsigned long long)(n + h);
 }
@@ -1666,7 +1670,8 @@ template <typename R>
 __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Prec<R>::C* wq,
                                             typename Prec<R>::C* vp, typename Prec<R>::C* vq, int h, int n,
                                             bool selfm, typename Prec<R>::T tol_abs,
-                                            typename Prec<R>::T col_floor, int lane, float& r2) {
+                                            typename Prec<R>::T col_floor, int lane, float& r2,
+                                            typename Prec<R>::T*, typename Prec<R>::T*) {
   typedef typename Prec<R>::C C;
   R al = 0, be = 0;
   C ga = zero_e<C>();
@@ -1751,33 +1756,51 @@ __device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, do
   }
 }
 
-// One-sided rotation of a column pair in double-float: the inner products by
-// compensated accumulation in every lane and a double-float butterfly, the rotation
-// parameters in FP64 from their FP64 roundings (as on the FP64 path: per pair, not
-// per element), the update of W and V in double-float.
+// Squared column norms after the rotation (c, s, e) of a pair with norms al, be and
+// inner product ga: with b~ = conj(e) b, a^dag b~ = |ga| = Re(conj(e) ga), so
+//   |a'|^2 = c^2 al + s^2 be - 2 c s |ga|,  |b'|^2 = s^2 al + c^2 be + 2 c s |ga|
+// (both rotation forms of ddc_rotate give these).  The double-float sweeps carry the
+// norms this way from pair to pair and recompute them at the start of every sweep,
+// so a sweep forms one inner product per pair instead of three.
+__device__ __forceinline__ void rotated_norms(double& al, double& be, double2 ga, double c, double s, double2 e) {
+  const double g = ga.x * e.x + ga.y * e.y, cc = c * c, ss = s * s, x = 2.0 * c * s * g;
+  const double a2 = cc * al + ss * be - x, b2 = ss * al + cc * be + x;
+  al = a2;
+  be = b2;
+}
+
+// One-sided rotation of a column pair in double-float: the inner product by
+// compensated accumulation in every lane and a double-float butterfly (the squared
+// column norms are carried by the caller), the rotation parameters in FP64 from their
+// FP64 roundings (as on the FP64 path: per pair, not per element), the update of W
+// and V in double-float.
 template <>
 __device__ __forceinline__ bool warp_rotate<dd>(ddc* wp, ddc* wq, ddc* vp, ddc* vq, int h, int n, bool selfm,
-                                                double tol_abs, double col_floor, int lane, float& r2) {
-  dd_acc al = dd_acc_zero(), be = dd_acc_zero(), gr = dd_acc_zero(), gi = dd_acc_zero();
+                                                double tol_abs, double col_floor, int lane, float& r2, double* np_,
+                                                double* nq_) {
+  // np_, nq_: the pair's squared column norms, carried from rotation to rotation
+  // (rotated_norms); read before the inner product, written by lane 0 after it
+  const double ald = *np_, bed = *nq_;
+  dd_acc gr = dd_acc_zero(), gi = dd_acc_zero();
   for (int x = lane; x < h; x += 32) {
     const ddc a = wp[x], b = wq[x];
-    dd_acc_mac(al, a.re, a.re);
-    dd_acc_mac(al, a.im, a.im);
-    dd_acc_mac(be, b.re, b.re);
-    dd_acc_mac(be, b.im, b.im);
     dd_acc_mac(gr, a.re, b.re);  // conj(a) b
     dd_acc_mac(gr, a.im, b.im);
     dd_acc_mac(gi, a.re, b.im);
     dd_acc_mac(gi, dd_neg(a.im), b.re);
   }
-  const double ald = dd_to(dd_warp_sum(dd_acc_value(al)));
-  const double bed = dd_to(dd_warp_sum(dd_acc_value(be)));
   const double2 ga = make_double2(dd_to(dd_warp_sum(dd_acc_value(gr))), dd_to(dd_warp_sum(dd_acc_value(gi))));
   r2 = (ald > col_floor && bed > col_floor) ? rel_off2(ald, bed, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y)
                                             : 0.f;
   double c, s;
   double2 e;
   if (!os_params(ald, bed, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
+  if (lane == 0) {
+    double a2 = ald, b2 = bed;
+    rotated_norms(a2, b2, ga, c, s, e);
+    *np_ = a2;
+    *nq_ = b2;
+  }
   ddc_rotate(wp, wq, h, lane, c, s, e);
   ddc_rotate(vp, vq, n, lane, c, s, e);
   return true;
@@ -1827,10 +1850,15 @@ __device__ R cluster_max_norm2(cg::cluster_group& cl, const typename Prec<R>::C*
 // V (n x n), column-major in global memory.  Returns the number of sweeps that
 // rotated; *rotations accumulates this CTA's applied rotations.
 template <typename R>
+// gN (double-float sweeps, where it is required; null otherwise): n squared column
+// norms in global memory, recomputed at the start of every sweep and carried through
+// it (staged with the block pair in the CTA's norm area of shared memory).
 __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, typename Prec<R>::C* gV, int n,
                               int h, bool selfm, typename Prec<R>::T tol_abs, typename Prec<R>::T col_floor,
-                              unsigned char* smem, const SvdLayout& L, int* hdr, unsigned long long* rotations) {
+                              unsigned char* smem, const SvdLayout& L, int* hdr, unsigned long long* rotations,
+                              typename Prec<R>::T* gN = nullptr) {
   typedef typename Prec<R>::C C;
+  typedef typename Prec<R>::T T;
   const int K = (int)cl.num_blocks(), kr = (int)cl.block_rank();
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const size_t room = L.total - L.data;
@@ -1843,11 +1871,22 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
   const bool v_st = w_st && (size_t)2 * b * ((size_t)h + n) * sizeof(C) <= room;
   C* sW = reinterpret_cast<C*>(smem + L.data);
   C* sV = sW + (size_t)2 * b * h;
+  T* sN = gN ? reinterpret_cast<T*>(smem + L.nrm) : nullptr;  // 2 b <= n <= D entries
   int sweep = 0;
   float wr2 = 0.f;  // this warp's largest relative off-diagonal^2 in the sweep
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     if (tid == 0) { hdr[HDR_ROT] = 0; hdr[HDR_RMAX] = 0; }
     wr2 = 0.f;
+    if constexpr (std::is_same<R, dd>::value) {
+      if (gN) {  // this CTA's share of the columns, read by every CTA after the barrier
+        const int c0 = (int)((long long)kr * n / K), c1 = (int)((long long)(kr + 1) * n / K);
+        for (int k = c0 + warp; k < c1; k += nwarp) {
+          const double v = ddc_col_norm2(gW + (long long)k * h, h, lane);
+          if (lane == 0) gN[k] = v;
+        }
+        cluster_exchange(cl);
+      }
+    }
     __syncthreads();
     for (int rho = 0; rho < nb - 1; ++rho) {
      for (int pi = kr; pi < nb / 2; pi += K) {
@@ -1861,8 +1900,8 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
       auto vcol = [&](int l) { return v_st ? sV + (size_t)l * n : gV + (long long)gcol(l) * n; };
       auto rotate = [&](int p, int q) {
         float r2 = 0.f;
-        const bool rot =
-            warp_rotate<R>(wcol(p), wcol(q), vcol(p), vcol(q), h, n, selfm, tol_abs, col_floor, lane, r2);
+        const bool rot = warp_rotate<R>(wcol(p), wcol(q), vcol(p), vcol(q), h, n, selfm, tol_abs, col_floor, lane,
+                                        r2, sN ? sN + p : nullptr, sN ? sN + q : nullptr);
         wr2 = fmaxf(wr2, r2);
         if (rot && lane == 0) atomicAdd(&hdr[HDR_ROT], 1);
       };
@@ -1871,6 +1910,8 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
         if (v_st)
           for (long long e = tid; e < (long long)nl * n; e += nth) sV[e] = gV[(long long)gcol((int)(e / n)) * n + e % n];
       }
+      if (sN)
+        for (int l = tid; l < nl; l += nth) sN[l] = gN[gcol(l)];
       __syncthreads();
       if (rho == 0) {
         // pairs inside each of the two blocks (every block is in exactly one pair of round 0)
@@ -1907,6 +1948,8 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
         if (v_st)
           for (long long e = tid; e < (long long)nl * n; e += nth) gV[(long long)gcol((int)(e / n)) * n + e % n] = sV[e];
       }
+      if (sN)
+        for (int l = tid; l < nl; l += nth) gN[gcol(l)] = sN[l];
       __syncthreads();  // the staging buffers are refilled for the next block pair
      }
       cluster_exchange(cl);
@@ -2109,7 +2152,7 @@ __device__ int polish_dd(cg::cluster_group& cl, const MpoDev& st, const Slot& sl
   cluster_exchange(cl);
   const double mx = cluster_max_norm2_dd(cl, Wd, h, k0, k1, hdr, reinterpret_cast<double*>(smem + L.nrm));
   const int sw = cluster_sweeps<dd>(cl, Wd, Vd, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, smem, L,
-                                    hdr, rot);
+                                    hdr, rot, reinterpret_cast<double*>(Sd));
   if (sw >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3600 + t);
   lap(CTR_CYC_POLISH);
   // singular values: column norms of W, ranked descending (ties by index)
@@ -2306,13 +2349,17 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
 // in FP64 from their FP64 roundings, one warp per pair applies the rotation in
 // double-float.  Same thresholds and stopping rule as the FP64 sweeps.
 __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, double tol_abs, double col_floor,
-                                PairWork<double>* pw, int* flags) {
+                                PairWork<double>* pw, int* flags, double* cnrm) {
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int np = n + (n & 1), half = np / 2;
   int sweep = 0;
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     __syncthreads();
     if (tid == 0) { flags[0] = 0; flags[2] = 0; }
+    for (int k = warp; k < n; k += nwarp) {  // squared column norms, carried through the sweep
+      const double v = ddc_col_norm2(W + (long long)k * h, h, lane);
+      if (lane == 0) cnrm[k] = v;
+    }
     __syncthreads();
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       for (int c0 = 0; c0 < half; c0 += PAIR_CHUNK) {
@@ -2323,23 +2370,17 @@ __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, doubl
           if (qq >= n) { if (lane == 0) pw[k].act = 0; continue; }
           const ddc* wp = W + (long long)p * h;
           const ddc* wq = W + (long long)qq * h;
-          dd_acc al = dd_acc_zero(), be = dd_acc_zero(), gr = dd_acc_zero(), gi = dd_acc_zero();
+          dd_acc gr = dd_acc_zero(), gi = dd_acc_zero();
           for (int x = lane; x < h; x += 32) {
             const ddc a = wp[x], b = wq[x];
-            dd_acc_mac(al, a.re, a.re);
-            dd_acc_mac(al, a.im, a.im);
-            dd_acc_mac(be, b.re, b.re);
-            dd_acc_mac(be, b.im, b.im);
             dd_acc_mac(gr, a.re, b.re);
             dd_acc_mac(gr, a.im, b.im);
             dd_acc_mac(gi, a.re, b.im);
             dd_acc_mac(gi, dd_neg(a.im), b.re);
           }
-          const double ald = dd_to(dd_warp_sum(dd_acc_value(al)));
-          const double bed = dd_to(dd_warp_sum(dd_acc_value(be)));
           const double gre = dd_to(dd_warp_sum(dd_acc_value(gr)));
           const double gim = dd_to(dd_warp_sum(dd_acc_value(gi)));
-          if (lane == 0) { pw[k].al = ald; pw[k].be = bed; pw[k].ga = make_double2(gre, gim); pw[k].act = 1; }
+          if (lane == 0) { pw[k].al = cnrm[p]; pw[k].be = cnrm[qq]; pw[k].ga = make_double2(gre, gim); pw[k].act = 1; }
         }
         __syncthreads();
         for (int k = tid; k < cn; k += nth) {
@@ -2356,6 +2397,12 @@ __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, doubl
             pw[k].c = c; pw[k].s = s; pw[k].e = e;
             flags[0] = 1;
             atomicAdd(&flags[1], 1);
+            int p, qq;  // each column is in one pair of the round: no other thread writes these
+            circle_pair(rnd, c0 + k, np, p, qq);
+            double a2 = al, b2 = be;
+            rotated_norms(a2, b2, pw[k].ga, c, s, e);
+            cnrm[p] = a2;
+            cnrm[qq] = b2;
           } else {
             pw[k].act = 0;
           }
@@ -2480,7 +2527,7 @@ __device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc
   for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
   __syncthreads();
   const int sweeps =
-      refine_sweeps_dd(W, Vc, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, pw, flags);
+      refine_sweeps_dd(W, Vc, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, pw, flags, nrm);
   if (sweeps >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
   for (int k = warp; k < n; k += nwarp) {
     const double a = ddc_col_norm2(W + (long long)k * h, h, lane);
@@ -2990,11 +3037,10 @@ __device__ void warp_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 // seed_max: the largest Gram side whose FP32 seed fits in one CTA's shared memory;
 // a larger block would run its whole Jacobi unseeded on one SM, so it always goes
 // to a cluster.
-__device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int min_n, int seed_max,
+__device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int min_n, int always_n, int seed_max,
                                           unsigned long long total, int ncta) {
   if (ws.big_min > 0) return n >= ws.big_min;
-  return n >= min_n &&
-         (n > seed_max || n >= SVD_CLUSTER_ALWAYS_N || svd_work(n, h) * (unsigned long long)ncta > total);
+  return n >= min_n && (n > seed_max || n >= always_n || svd_work(n, h) * (unsigned long long)ncta > total);
 }
 
 // category: 0 cluster, 1 one CTA, 2 one warp in a quarter slice, 3 one warp in an
@@ -3003,12 +3049,12 @@ __device__ __forceinline__ int order_key(int cat, int n, int h) {
   return cat * 64 + 63 - min(63, (int)log2((double)svd_work(n, h) + 1.0));
 }
 
-// ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block;
-// room: the shared memory a CTA has for block data on the FP32 path (0: the FP64 path,
-// no warp blocks).  counter: cursor and end of the cluster ([0], [1]), CTA ([2], [3]),
+// ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block; always_n:
+// the Gram side from which every block goes to a cluster; room: the shared memory a
+// CTA has for block data on the FP32 path (0: the FP64 path, no warp blocks).  counter: cursor and end of the cluster ([0], [1]), CTA ([2], [3]),
 // quarter-slice warp ([4], [5]) and eighth-slice warp ([6], [7]) parts of list.
 __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter, int ncta,
-                                                int min_n, int seed_max, int room) {
+                                                int min_n, int always_n, int seed_max, int room) {
   __shared__ int hist[256], start[256];
   __shared__ unsigned long long total;
   const int tid = threadIdx.x, lane = tid & 31, Pc = ws.Pc, E = ngates * Pc;
@@ -3038,7 +3084,7 @@ __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list
   const unsigned long long tot = total;
   const size_t eighth = (((size_t)room / SVD_WARPS) & ~(size_t)15), quarter = (((size_t)room / 4) & ~(size_t)15);
   auto category = [&](int n, int h) {
-    if (route_big(ws, n, h, min_n, seed_max, tot, ncta)) return 0;
+    if (route_big(ws, n, h, min_n, always_n, seed_max, tot, ncta)) return 0;
     // a block on the layer's critical path keeps a whole CTA (lower latency than one warp)
     const bool critical = svd_work(n, h) * (unsigned long long)ncta > tot;
     if (room > 0 && n <= WARP_SVD_N && !critical) {
@@ -3640,7 +3686,8 @@ void launch_layer_t(const MpoDev& s, const SlotWS& ws, const GateDesc* d_gates, 
   const int room = sizeof(R) == 4 ? (int)(SL.total - SL.data) : 0;
   {
     NvtxRange r("gbs_mpo/k_order");
-    k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, seed_max, room);
+    k_order<<<1, 1024, 0, st>>>(ws, ngates, ws.list, ws.counter, svd_ctas, SvdRoute<R>::min_n, SvdRoute<R>::always_n,
+                                seed_max, room);
   }
   if (ev) record_stage_event(ev[4], st);
   { NvtxRange r("gbs_mpo/k_svd"); launch_svd<R>(s, ws, d_gates, svd_ctas, K, st); }
