@@ -3051,8 +3051,9 @@ __device__ __forceinline__ int order_key(int cat, int n, int h) {
 
 // ncta: CTAs of the k_svd launch; min_n: the path's smallest cluster block; always_n:
 // the Gram side from which every block goes to a cluster; room: the shared memory a
-// CTA has for block data on the FP32 path (0: the FP64 path, no warp blocks).  counter: cursor and end of the cluster ([0], [1]), CTA ([2], [3]),
-// quarter-slice warp ([4], [5]) and eighth-slice warp ([6], [7]) parts of list.
+// CTA has for block data on the FP32 path (0: the FP64 path, no warp blocks).
+// counter: cursor and end of the cluster ([0], [1]), CTA ([2], [3]), quarter-slice
+// warp ([4], [5]) and eighth-slice warp ([6], [7]) parts of list.
 __global__ void __launch_bounds__(1024) k_order(SlotWS ws, int ngates, int* list, int* counter, int ncta,
                                                 int min_n, int always_n, int seed_max, int room) {
   __shared__ int hist[256], start[256];
