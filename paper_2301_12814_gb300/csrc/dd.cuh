@@ -35,11 +35,13 @@
 #define DD_SUB(a, b) __fsub_rn((a), (b))
 #define DD_MUL(a, b) __fmul_rn((a), (b))
 #define DD_FMA(a, b, c) __fmaf_rn((a), (b), (c))
+#define DD_RSQRT(a) rsqrtf(a)
 #else
 #define DD_ADD(a, b) ((a) + (b))
 #define DD_SUB(a, b) ((a) - (b))
 #define DD_MUL(a, b) ((a) * (b))
 #define DD_FMA(a, b, c) fmaf((a), (b), (c))
+#define DD_RSQRT(a) (1.0f / sqrtf(a))
 #endif
 
 struct dd {
@@ -100,6 +102,17 @@ __host__ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   float s, r;
   fast_two_sum(p, e, s, r);
   return dd_make(s, r);
+}
+
+// 1 / sqrt(x) for a double-float x > 0 (x.hi a normal FP32 number): the FP32 estimate
+// y0 and one Newton step y = y0 + y0 (1 - x y0^2) / 2, with 1 - x y0^2 formed in
+// double-float (y0^2 exactly by TwoProd).  The step squares the estimate's relative
+// error (~2^-22 -> ~2^-44), about the accuracy of a double-float.
+__host__ __device__ __forceinline__ dd dd_rsqrt(dd x) {
+  const float y0 = DD_RSQRT(x.hi);
+  const float p = DD_MUL(y0, y0), pe = DD_FMA(y0, y0, -p);
+  const dd r = dd_sub(dd_make(1.f, 0.f), dd_mul(x, dd_make(p, pe)));
+  return dd_add_f(dd_make(y0, 0.f), DD_MUL(DD_MUL(0.5f, y0), r.hi));
 }
 
 // c x + s y for real double-floats

@@ -1732,10 +1732,10 @@ constexpr double DD_SMALL_ROT = 1e-7;
 // parts: |dx|, |dy| <= ~1e-7 |x, y|, so the FP32 rounding and the neglected low parts
 // stay near 1e-14 relative, and an element costs a TwoSum per component instead of two
 // double-float products.
-__device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, double c, double s, double2 e) {
-  if (fabs(s) < DD_SMALL_ROT) {
-    const float cm1 = (float)(c - 1.0), sf = (float)s;
-    const float er = (float)e.x, ei = (float)e.y;
+__device__ __forceinline__ void ddc_rotate_dd(ddc* x, ddc* y, int len, int lane, dd c, dd s, ddc e) {
+  if (fabsf(s.hi) < (float)DD_SMALL_ROT) {
+    const float cm1 = (c.hi - 1.f) + c.lo, sf = s.hi;  // c.hi - 1 is exact (Sterbenz)
+    const float er = e.re.hi, ei = e.im.hi;
     for (int k = lane; k < len; k += 32) {
       const ddc a = x[k], b = y[k];
       const float ceb_r = er * b.re.hi + ei * b.im.hi, ceb_i = er * b.im.hi - ei * b.re.hi;  // conj(e) b
@@ -1747,13 +1747,16 @@ __device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, do
     }
     return;
   }
-  const dd cd = dd_from(c), sd = dd_from(s), msd = dd_neg(sd);
-  const ddc ec = ddc_from(e.x, -e.y);
+  const dd msd = dd_neg(s);
+  const ddc ec = ddc_conj(e);
   for (int k = lane; k < len; k += 32) {
     const ddc a = x[k], bs = ddc_mul(y[k], ec);
-    x[k] = ddc_lin(cd, a, msd, bs);
-    y[k] = ddc_lin(sd, a, cd, bs);
+    x[k] = ddc_lin(c, a, msd, bs);
+    y[k] = ddc_lin(s, a, c, bs);
   }
+}
+__device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, double c, double s, double2 e) {
+  ddc_rotate_dd(x, y, len, lane, dd_from(c), dd_from(s), ddc_from(e.x, e.y));
 }
 
 // Squared column norms after the rotation (c, s, e) of a pair with norms al, be and
@@ -1769,6 +1772,60 @@ __device__ __forceinline__ void rotated_norms(double& al, double& be, double2 ga
   be = b2;
 }
 
+// Rotation parameters of a double-float column pair on the FP32 pipe (GB300 runs FP64
+// at 1/61 of the FP32 rate, and the cluster sweeps form them in every lane of the
+// pair's warp).  The same decision and angle as os_params: rotate when both columns
+// are above the floor and |g| exceeds tol_abs and os_rel sqrt(al be); tau =
+// (be - al) / 2|g| with be - al in double-float, t = tan(angle) rounded to FP32.  Then
+// c = 1 / sqrt(1 + t^2) and s = t c in double-float (1 + t^2 exact, dd_rsqrt), and the
+// unit phase e = g / |g| in double-float from g scaled by a power of two (exact) so
+// that |g|^2 neither underflows nor overflows.  r2 = |g|^2 / (al be) for the sweep stop.
+__device__ __forceinline__ float pow2_recip(float m) {  // 2^-E with m in [2^E, 2^(E+1)), m > 0 finite
+  const int ex = (__float_as_int(m) >> 23) & 0xff;
+  return __int_as_float((254 - (ex > 0 ? ex : 1)) << 23);
+}
+__device__ __forceinline__ bool dd_os_params(dd al, dd be, dd gr, dd gi, bool selfm, float tol_abs, float col_floor,
+                                             dd& c, dd& s, ddc& e, dd& gabs, float& r2) {
+  if (selfm) gi = dd_zero();
+  const float a = al.hi, b = be.hi;
+  const float gf = selfm ? fabsf(gr.hi) : hypotf(gr.hi, gi.hi);
+  const bool above = a > col_floor && b > col_floor;
+  const float rel = above ? gf * rsqrtf(a) * rsqrtf(b) : 0.f;
+  r2 = rel * rel;
+  if (!(above && gf > tol_abs && rel > (float)Prec<double>::os_rel)) return false;
+  const float tau = 0.5f * dd_sub(be, al).hi / gf;
+  if (!(fabsf(tau) < 1e30f)) return false;  // angle below any representable rotation
+  const float af = fabsf(tau);
+  const float t = (tau >= 0.f ? 1.f : -1.f) * (af > 1e4f ? 0.5f / af : 1.f / (af + sqrtf(1.f + tau * tau)));
+  const float p = __fmul_rn(t, t), pe = __fmaf_rn(t, t, -p);
+  c = dd_rsqrt(dd_add_f(dd_add_f(dd_make(1.f, 0.f), p), pe));
+  s = dd_mul(dd_make(t, 0.f), c);
+  if (selfm) {
+    const bool neg = gr.hi < 0.f;
+    e = ddc_make(dd_make(neg ? -1.f : 1.f, 0.f), dd_zero());
+    gabs = neg ? dd_neg(gr) : gr;
+  } else {
+    const float sc = pow2_recip(fmaxf(fabsf(gr.hi), fabsf(gi.hi))), isc = 1.f / sc;
+    const dd xr = dd_make(gr.hi * sc, gr.lo * sc), xi = dd_make(gi.hi * sc, gi.lo * sc);
+    const dd g2 = dd_add(dd_mul(xr, xr), dd_mul(xi, xi));  // in [1, 8)
+    const dd inv = dd_rsqrt(g2);
+    e = ddc_make(dd_mul(xr, inv), dd_mul(xi, inv));
+    const dd gs = dd_mul(g2, inv);
+    gabs = dd_make(gs.hi * isc, gs.lo * isc);
+  }
+  return true;
+}
+// Squared column norms after the rotation (c, s, e) (see rotated_norms), in double-float.
+__device__ __forceinline__ void rotated_norms_dd(dd& al, dd& be, dd gabs, dd c, dd s) {
+  const dd cc = dd_mul(c, c), ss = dd_mul(s, s);
+  dd x = dd_mul(dd_mul(c, s), gabs);
+  x = dd_add(x, x);
+  const dd a2 = dd_sub(dd_add(dd_mul(cc, al), dd_mul(ss, be)), x);
+  const dd b2 = dd_add(dd_add(dd_mul(ss, al), dd_mul(cc, be)), x);
+  al = a2;
+  be = b2;
+}
+
 // One-sided rotation of a column pair in double-float: the inner product by
 // compensated accumulation in every lane and a double-float butterfly (the squared
 // column norms are carried by the caller), the rotation parameters in FP64 from their
@@ -1778,9 +1835,12 @@ template <>
 __device__ __forceinline__ bool warp_rotate<dd>(ddc* wp, ddc* wq, ddc* vp, ddc* vq, int h, int n, bool selfm,
                                                 double tol_abs, double col_floor, int lane, float& r2, double* np_,
                                                 double* nq_) {
-  // np_, nq_: the pair's squared column norms, carried from rotation to rotation
-  // (rotated_norms); read before the inner product, written by lane 0 after it
-  const double ald = *np_, bed = *nq_;
+  // np_, nq_: the pair's squared column norms as double-floats (8 bytes, like the
+  // double they are stored as), carried from rotation to rotation; read before the
+  // inner product, written by lane 0 after it
+  dd* pn = reinterpret_cast<dd*>(np_);
+  dd* qn = reinterpret_cast<dd*>(nq_);
+  const dd al = *pn, be = *qn;
   dd_acc gr = dd_acc_zero(), gi = dd_acc_zero();
   for (int x = lane; x < h; x += 32) {
     const ddc a = wp[x], b = wq[x];
@@ -1789,25 +1849,33 @@ __device__ __forceinline__ bool warp_rotate<dd>(ddc* wp, ddc* wq, ddc* vp, ddc* 
     dd_acc_mac(gi, a.re, b.im);
     dd_acc_mac(gi, dd_neg(a.im), b.re);
   }
-  const double2 ga = make_double2(dd_to(dd_warp_sum(dd_acc_value(gr))), dd_to(dd_warp_sum(dd_acc_value(gi))));
-  r2 = (ald > col_floor && bed > col_floor) ? rel_off2(ald, bed, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y)
-                                            : 0.f;
-  double c, s;
-  double2 e;
-  if (!os_params(ald, bed, ga, selfm, tol_abs, col_floor, c, s, e)) return false;
+  const dd g_re = dd_warp_sum(dd_acc_value(gr)), g_im = dd_warp_sum(dd_acc_value(gi));
+  dd c, s, gabs;
+  ddc e;
+  if (!dd_os_params(al, be, g_re, g_im, selfm, (float)tol_abs, (float)col_floor, c, s, e, gabs, r2)) return false;
   if (lane == 0) {
-    double a2 = ald, b2 = bed;
-    rotated_norms(a2, b2, ga, c, s, e);
-    *np_ = a2;
-    *nq_ = b2;
+    dd a2 = al, b2 = be;
+    rotated_norms_dd(a2, b2, gabs, c, s);
+    *pn = a2;
+    *qn = b2;
   }
-  ddc_rotate(wp, wq, h, lane, c, s, e);
-  ddc_rotate(vp, vq, n, lane, c, s, e);
+  ddc_rotate_dd(wp, wq, h, lane, c, s, e);
+  ddc_rotate_dd(vp, vq, n, lane, c, s, e);
   return true;
 }
 
 // Squared norm of a column of length len, in double-float by one warp (every lane
-// gets the FP64 rounding of the same value).
+// gets the same value).
+__device__ __forceinline__ dd ddc_col_norm2_dd(const ddc* w, int len, int lane) {
+  dd_acc a = dd_acc_zero();
+  for (int x = lane; x < len; x += 32) {
+    const ddc v = w[x];
+    dd_acc_mac(a, v.re, v.re);
+    dd_acc_mac(a, v.im, v.im);
+  }
+  return dd_warp_sum(dd_acc_value(a));
+}
+// The same, rounded to FP64.
 __device__ __forceinline__ double ddc_col_norm2(const ddc* w, int len, int lane) {
   dd_acc a = dd_acc_zero();
   for (int x = lane; x < len; x += 32) {
@@ -1880,9 +1948,9 @@ __device__ int cluster_sweeps(cg::cluster_group& cl, typename Prec<R>::C* gW, ty
     if constexpr (std::is_same<R, dd>::value) {
       if (gN) {  // this CTA's share of the columns, read by every CTA after the barrier
         const int c0 = (int)((long long)kr * n / K), c1 = (int)((long long)(kr + 1) * n / K);
-        for (int k = c0 + warp; k < c1; k += nwarp) {
-          const double v = ddc_col_norm2(gW + (long long)k * h, h, lane);
-          if (lane == 0) gN[k] = v;
+        for (int k = c0 + warp; k < c1; k += nwarp) {  // stored as double-floats (see warp_rotate<dd>)
+          const dd v = ddc_col_norm2_dd(gW + (long long)k * h, h, lane);
+          if (lane == 0) reinterpret_cast<dd*>(gN)[k] = v;
         }
         cluster_exchange(cl);
       }

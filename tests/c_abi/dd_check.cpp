@@ -4,8 +4,8 @@
 // Reference values come from long double (64-bit significand on x86-64, 113-bit on
 // AArch64), exact for the products and sums checked here to well below the ~2^-47
 // accuracy of a double-float.  Checked over random inputs spanning 2^-40..2^40, with
-// cancellation: dd_add, dd_add_f (a double-float plus an FP32 correction), dd_mul, the
-// complex product, c x + s y, and the compensated dot product
+// cancellation: dd_add, dd_add_f (a double-float plus an FP32 correction), dd_mul,
+// dd_rsqrt, the complex product, c x + s y, and the compensated dot product
 // over 16-term chains combined pairwise with dd_add (the Jacobi inner products: h rows
 // split over 32 lanes, then a butterfly).  Prints the worst relative errors (to the
 // magnitude sum for dot products) and exits 1 if one exceeds its bound.
@@ -61,6 +61,13 @@ int main() {
     const LD ex = val(a) + (LD)f, sc = fabsl(val(a)) + fabsl((LD)f);
     if (sc > 0) w_addf = std::fmax(w_addf, (double)(fabsl(val(dd_add_f(a, f)) - ex) / sc));
   }
+  double w_rsq = 0;
+  for (int t = 0; t < 200000; ++t) {  // 1 / sqrt(x): rotation cosines and unit phases
+    std::uniform_real_distribution<double> u1(0.0, 1.0), ex(-60.0, 60.0);
+    const dd x = dd_from(std::ldexp(0.5 + u1(g), (int)ex(g)));
+    const LD ex_v = 1.0L / sqrtl(val(x));
+    w_rsq = std::fmax(w_rsq, (double)(fabsl(val(dd_rsqrt(x)) - ex_v) / ex_v));
+  }
   std::normal_distribution<double> nd(0.0, 1.0);
   for (int t = 0; t < 2000; ++t) {
     // 32 lanes x 16 terms of a unit-scale dot product, lane sums combined pairwise
@@ -81,10 +88,11 @@ int main() {
     w_dot = std::fmax(w_dot, (double)(fabsl(val(part[0]) - exact) / mag));
   }
   const double u = std::ldexp(1.0, -24);
-  std::printf("add %.3e add_f %.3e mul %.3e cmul %.3e lin %.3e dot %.3e (units of u^2: %.1f %.1f %.1f %.1f %.1f %.1f)\n",
-              w_add, w_addf, w_mul, w_cmul, w_lin, w_dot, w_add / (u * u), w_addf / (u * u), w_mul / (u * u),
-              w_cmul / (u * u), w_lin / (u * u), w_dot / (u * u));
-  const bool ok = w_add <= 4 * u * u && w_addf <= 4 * u * u && w_mul <= 8 * u * u && w_cmul <= 16 * u * u &&
-                  w_lin <= 16 * u * u && w_dot <= 64 * u * u;
+  std::printf("add %.3e add_f %.3e mul %.3e rsqrt %.3e cmul %.3e lin %.3e dot %.3e "
+              "(units of u^2: %.1f %.1f %.1f %.1f %.1f %.1f %.1f)\n",
+              w_add, w_addf, w_mul, w_rsq, w_cmul, w_lin, w_dot, w_add / (u * u), w_addf / (u * u), w_mul / (u * u),
+              w_rsq / (u * u), w_cmul / (u * u), w_lin / (u * u), w_dot / (u * u));
+  const bool ok = w_add <= 4 * u * u && w_addf <= 4 * u * u && w_mul <= 8 * u * u && w_rsq <= 16 * u * u &&
+                  w_cmul <= 16 * u * u && w_lin <= 16 * u * u && w_dot <= 64 * u * u;
   return ok ? 0 : 1;
 }
