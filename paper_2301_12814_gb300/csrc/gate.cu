@@ -58,11 +58,14 @@ constexpr int JACOBI_MAX_SWEEPS = 60;
 // path, and the large ones.  A block goes to a cluster when its Gram side is at least
 // min_n and either its Jacobi work estimate n^2 (n + h) exceeds the layer's total over
 // the CTAs of k_svd (it alone would hold one SM longer than the average SM is busy),
-// or its Gram side is at least always_n (on one CTA such a block costs more SM-time
-// than on a cluster).  A throughput-bound layer of small blocks (many instances)
-// therefore keeps every block on one CTA.  Measured on GB300, s per mesh with every
-// block from a Gram side n0 up on a cluster and no other (the load rule alone sent
-// blocks there from about 110 at 48 modes and about 60 at 32 modes):
+// or its Gram side is at least always_n and its work at least 1/16 of that average
+// (on one CTA such a block costs more SM-time than on a cluster, unless the layer has
+// work enough to keep every SM busy without it: the 64-instance batched mesh lost
+// 2.4 % with its blocks from 48 up on clusters).  A throughput-bound layer of small
+// blocks (many instances) therefore keeps every block on one CTA.  Measured on GB300,
+// s per mesh with every block from a Gram side n0 up on a cluster and no other (the
+// load rule alone sent blocks there from about 110 at 48 modes and about 60 at 32
+// modes):
 //   n0                       48     64     80     96     112    128    load rule
 //   48 modes chi 512 FP64   4.23   4.24   4.46   4.51   5.31   5.72   4.51
 //   48 modes chi 512 TF32   1.33   1.26   1.31   1.35   1.46   1.57   1.35
@@ -1672,6 +1675,9 @@ __device__ __forceinline__ bool warp_rotate(typename Prec<R>::C* wp, typename Pr
                                             bool selfm, typename Prec<R>::T tol_abs,
                                             typename Prec<R>::T col_floor, int lane, float& r2,
                                             typename Prec<R>::T*, typename Prec<R>::T*) {
+  // (the FP32 sweeps recompute both column norms for every pair: carrying them as the
+  // double-float sweeps do was measured slower, 4.2 against 3.8 ms of FP32 phase per
+  // 48-mode cluster block, with a recompute of norms that a rotation shrinks)
   typedef typename Prec<R>::C C;
   R al = 0, be = 0;
   C ga = zero_e<C>();
@@ -1719,7 +1725,7 @@ __device__ __forceinline__ dd dd_warp_sum(dd v) {
 __device__ __forceinline__ ddc ddc_conv(double2 a) { return ddc_from(a.x, a.y); }
 __device__ __forceinline__ double2 ddc_back(ddc a) { return make_double2(dd_to(a.re), dd_to(a.im)); }
 
-// Rotation angles below this apply through FP32 corrections (ddc_rotate).
+// Rotation angles below this apply through FP32 corrections (ddc_rotate_dd).
 constexpr double DD_SMALL_ROT = 1e-7;
 
 // Apply the rotation (c, s, e) to the column pair (x, y) in double-float, elements
@@ -1755,22 +1761,7 @@ __device__ __forceinline__ void ddc_rotate_dd(ddc* x, ddc* y, int len, int lane,
     y[k] = ddc_lin(s, a, c, bs);
   }
 }
-__device__ __forceinline__ void ddc_rotate(ddc* x, ddc* y, int len, int lane, double c, double s, double2 e) {
-  ddc_rotate_dd(x, y, len, lane, dd_from(c), dd_from(s), ddc_from(e.x, e.y));
-}
 
-// Squared column norms after the rotation (c, s, e) of a pair with norms al, be and
-// inner product ga: with b~ = conj(e) b, a^dag b~ = |ga| = Re(conj(e) ga), so
-//   |a'|^2 = c^2 al + s^2 be - 2 c s |ga|,  |b'|^2 = s^2 al + c^2 be + 2 c s |ga|
-// (both rotation forms of ddc_rotate give these).  The double-float sweeps carry the
-// norms this way from pair to pair and recompute them at the start of every sweep,
-// so a sweep forms one inner product per pair instead of three.
-__device__ __forceinline__ void rotated_norms(double& al, double& be, double2 ga, double c, double s, double2 e) {
-  const double g = ga.x * e.x + ga.y * e.y, cc = c * c, ss = s * s, x = 2.0 * c * s * g;
-  const double a2 = cc * al + ss * be - x, b2 = ss * al + cc * be + x;
-  al = a2;
-  be = b2;
-}
 
 // Rotation parameters of a double-float column pair on the FP32 pipe (GB300 runs FP64
 // at 1/61 of the FP32 rate, and the cluster sweeps form them in every lane of the
@@ -1815,7 +1806,12 @@ __device__ __forceinline__ bool dd_os_params(dd al, dd be, dd gr, dd gi, bool se
   }
   return true;
 }
-// Squared column norms after the rotation (c, s, e) (see rotated_norms), in double-float.
+// Squared column norms after the rotation (c, s, e) of a pair with norms al, be and
+// inner product g: with b~ = conj(e) b, a^dag b~ = |g|, so
+//   |a'|^2 = c^2 al + s^2 be - 2 c s |g|,  |b'|^2 = s^2 al + c^2 be + 2 c s |g|
+// (both rotation forms of ddc_rotate_dd give these).  The double-float sweeps carry the
+// norms this way from pair to pair and recompute them at the start of every sweep,
+// so a sweep forms one inner product per pair instead of three.
 __device__ __forceinline__ void rotated_norms_dd(dd& al, dd& be, dd gabs, dd c, dd s) {
   const dd cc = dd_mul(c, c), ss = dd_mul(s, s);
   dd x = dd_mul(dd_mul(c, s), gabs);
@@ -2413,19 +2409,27 @@ __device__ void big_block(cg::cluster_group& cl, const MpoDev& st, const Slot& s
 
 // ---------------------------------------------------------------- double-float refinement (FP64 path, one CTA)
 // refine_sweeps in double-float arithmetic: per round, one warp per pair forms the
-// inner products (compensated, dd.cuh), one thread per pair the rotation parameters
-// in FP64 from their FP64 roundings, one warp per pair applies the rotation in
-// double-float.  Same thresholds and stopping rule as the FP64 sweeps.
+// inner product (compensated, dd.cuh; the squared column norms are carried through
+// the sweep and recomputed at its start), one thread per pair the rotation parameters
+// and the new norms on the FP32 pipe (dd_os_params), one warp per pair applies the
+// rotation in double-float.  Same thresholds and stopping rule as the FP64 sweeps.
+struct PairWorkDD {
+  dd gr, gi, c, s;
+  ddc e;
+  int act;
+};
+static_assert(sizeof(PairWorkDD) <= sizeof(PairWork<double>), "pair work area");
 __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, double tol_abs, double col_floor,
-                                PairWork<double>* pw, int* flags, double* cnrm) {
+                                PairWorkDD* pw, int* flags, dd* cnrm) {
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   const int np = n + (n & 1), half = np / 2;
+  const float tol_f = (float)tol_abs, floor_f = (float)col_floor;
   int sweep = 0;
   for (; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     __syncthreads();
     if (tid == 0) { flags[0] = 0; flags[2] = 0; }
     for (int k = warp; k < n; k += nwarp) {  // squared column norms, carried through the sweep
-      const double v = ddc_col_norm2(W + (long long)k * h, h, lane);
+      const dd v = ddc_col_norm2_dd(W + (long long)k * h, h, lane);
       if (lane == 0) cnrm[k] = v;
     }
     __syncthreads();
@@ -2446,31 +2450,26 @@ __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, doubl
             dd_acc_mac(gi, a.re, b.im);
             dd_acc_mac(gi, dd_neg(a.im), b.re);
           }
-          const double gre = dd_to(dd_warp_sum(dd_acc_value(gr)));
-          const double gim = dd_to(dd_warp_sum(dd_acc_value(gi)));
-          if (lane == 0) { pw[k].al = cnrm[p]; pw[k].be = cnrm[qq]; pw[k].ga = make_double2(gre, gim); pw[k].act = 1; }
+          const dd g_re = dd_warp_sum(dd_acc_value(gr)), g_im = dd_warp_sum(dd_acc_value(gi));
+          if (lane == 0) { pw[k].gr = g_re; pw[k].gi = g_im; pw[k].act = 1; }
         }
         __syncthreads();
         for (int k = tid; k < cn; k += nth) {
           if (!pw[k].act) continue;
-          const double al = pw[k].al, be = pw[k].be;
-          if (al > col_floor && be > col_floor) {
-            const double2 ga = pw[k].ga;
-            const float r2 = rel_off2(al, be, selfm ? ga.x * ga.x : ga.x * ga.x + ga.y * ga.y);
-            atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(r2));
-          }
-          double c, s;
-          double2 e;
-          if (os_params(al, be, pw[k].ga, selfm, tol_abs, col_floor, c, s, e)) {
+          int p, qq;  // each column is in one pair of the round: no other thread touches its norm
+          circle_pair(rnd, c0 + k, np, p, qq);
+          dd al = cnrm[p], be = cnrm[qq], c, s, gabs;
+          ddc e;
+          float r2 = 0.f;
+          const bool rot = dd_os_params(al, be, pw[k].gr, pw[k].gi, selfm, tol_f, floor_f, c, s, e, gabs, r2);
+          atomicMax(reinterpret_cast<unsigned*>(&flags[2]), __float_as_uint(r2));
+          if (rot) {
             pw[k].c = c; pw[k].s = s; pw[k].e = e;
             flags[0] = 1;
             atomicAdd(&flags[1], 1);
-            int p, qq;  // each column is in one pair of the round: no other thread writes these
-            circle_pair(rnd, c0 + k, np, p, qq);
-            double a2 = al, b2 = be;
-            rotated_norms(a2, b2, pw[k].ga, c, s, e);
-            cnrm[p] = a2;
-            cnrm[qq] = b2;
+            rotated_norms_dd(al, be, gabs, c, s);
+            cnrm[p] = al;
+            cnrm[qq] = be;
           } else {
             pw[k].act = 0;
           }
@@ -2480,8 +2479,8 @@ __device__ int refine_sweeps_dd(ddc* W, ddc* Vc, int n, int h, bool selfm, doubl
           if (!pw[k].act) continue;
           int p, qq;
           circle_pair(rnd, c0 + k, np, p, qq);
-          ddc_rotate(W + (long long)p * h, W + (long long)qq * h, h, lane, pw[k].c, pw[k].s, pw[k].e);
-          ddc_rotate(Vc + (long long)p * n, Vc + (long long)qq * n, n, lane, pw[k].c, pw[k].s, pw[k].e);
+          ddc_rotate_dd(W + (long long)p * h, W + (long long)qq * h, h, lane, pw[k].c, pw[k].s, pw[k].e);
+          ddc_rotate_dd(Vc + (long long)p * n, Vc + (long long)qq * n, n, lane, pw[k].c, pw[k].s, pw[k].e);
         }
         __syncthreads();
       }
@@ -2506,7 +2505,7 @@ __device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   int* flags = reinterpret_cast<int*>(smem + L.hdr);
   double* nrm = reinterpret_cast<double*>(smem + L.nrm);
-  PairWork<double>* pw = reinterpret_cast<PairWork<double>*>(smem + L.pw);
+  PairWorkDD* pw = reinterpret_cast<PairWorkDD*>(smem + L.pw);  // smaller than PairWork<double>
   const size_t room = L.total - L.data;
   const bool w_smem = (size_t)h * n * sizeof(ddc) <= room;
   const bool in_smem = ((size_t)h * n + (size_t)n * n) * sizeof(ddc) <= room;
@@ -2595,7 +2594,8 @@ __device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc
   for (int w2 = 0; w2 < nwarp; ++w2) mx = fmax(mx, nrm[w2]);
   __syncthreads();
   const int sweeps =
-      refine_sweeps_dd(W, Vc, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, pw, flags, nrm);
+      refine_sweeps_dd(W, Vc, n, h, selfm, Prec<dd>::os_abs * mx, Prec<dd>::floor * mx, pw, flags,
+                       reinterpret_cast<dd*>(nrm));
   if (sweeps >= JACOBI_MAX_SWEEPS && tid == 0) dev_set_error(st.err, DEV_ERR_NUMERIC, 3500 + t);
   for (int k = warp; k < n; k += nwarp) {
     const double a = ddc_col_norm2(W + (long long)k * h, h, lane);
@@ -3108,7 +3108,8 @@ __device__ void warp_block(const MpoDev& st, const Slot& sl, const GateDesc& g, 
 __device__ __forceinline__ bool route_big(const SlotWS& ws, int n, int h, int min_n, int always_n, int seed_max,
                                           unsigned long long total, int ncta) {
   if (ws.big_min > 0) return n >= ws.big_min;
-  return n >= min_n && (n > seed_max || n >= always_n || svd_work(n, h) * (unsigned long long)ncta > total);
+  const unsigned long long w = svd_work(n, h) * (unsigned long long)ncta;
+  return n >= min_n && (n > seed_max || w > total || (n >= always_n && 16ull * w > total));
 }
 
 // category: 0 cluster, 1 one CTA, 2 one warp in a quarter slice, 3 one warp in an
