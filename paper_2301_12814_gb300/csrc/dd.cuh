@@ -105,14 +105,17 @@ __host__ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
 }
 
 // 1 / sqrt(x) for a double-float x > 0 (x.hi a normal FP32 number): the FP32 estimate
-// y0 and one Newton step y = y0 + y0 (1 - x y0^2) / 2, with 1 - x y0^2 formed in
-// double-float (y0^2 exactly by TwoProd).  The step squares the estimate's relative
-// error (~2^-22 -> ~2^-44), about the accuracy of a double-float.
+// y0 and two Newton steps y <- y + y (1 - x y^2) / 2, with 1 - x y^2 formed in
+// double-float.  Each step squares the relative error (the estimate's 2^-22 at most,
+// then ~2^-43, then the double-float rounding of the last step): rotation cosines and
+// unit phases built on it stay unitary to a few u^2.
 __host__ __device__ __forceinline__ dd dd_rsqrt(dd x) {
-  const float y0 = DD_RSQRT(x.hi);
-  const float p = DD_MUL(y0, y0), pe = DD_FMA(y0, y0, -p);
-  const dd r = dd_sub(dd_make(1.f, 0.f), dd_mul(x, dd_make(p, pe)));
-  return dd_add_f(dd_make(y0, 0.f), DD_MUL(DD_MUL(0.5f, y0), r.hi));
+  dd y = dd_make(DD_RSQRT(x.hi), 0.f);
+  for (int it = 0; it < 2; ++it) {
+    const dd r = dd_sub(dd_make(1.f, 0.f), dd_mul(x, dd_mul(y, y)));
+    y = dd_add_f(y, DD_MUL(DD_MUL(0.5f, y.hi), r.hi));
+  }
+  return y;
 }
 
 // c x + s y for real double-floats

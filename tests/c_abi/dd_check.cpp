@@ -92,7 +92,7 @@ int main() {
               "(units of u^2: %.1f %.1f %.1f %.1f %.1f %.1f %.1f)\n",
               w_add, w_addf, w_mul, w_rsq, w_cmul, w_lin, w_dot, w_add / (u * u), w_addf / (u * u), w_mul / (u * u),
               w_rsq / (u * u), w_cmul / (u * u), w_lin / (u * u), w_dot / (u * u));
-  const bool ok = w_add <= 4 * u * u && w_addf <= 4 * u * u && w_mul <= 8 * u * u && w_rsq <= 16 * u * u &&
+  const bool ok = w_add <= 4 * u * u && w_addf <= 4 * u * u && w_mul <= 8 * u * u && w_rsq <= 4 * u * u &&
                   w_cmul <= 16 * u * u && w_lin <= 16 * u * u && w_dot <= 64 * u * u;
   return ok ? 0 : 1;
 }
