@@ -620,6 +620,14 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
   // the CTA's P buffers)
   int* shn = reinterpret_cast<int*>(tsm + TL.misc);  // [0] nc, [1] nm of the current large item
   C* accs = reinterpret_cast<C*>(tsm + TL.pbuf);
+  // FP64 path: the large items contract in double-float arithmetic on the FP32 pipe
+  // (GB300's FP64 rate is 1/61 of its FP32 rate), with the Fock table as double-floats
+  // behind the two staged tiles (the P buffers are free until the small items)
+  ddc* fkd = reinterpret_cast<ddc*>(accs + 2 * TILE * (TILE + 1));
+  if constexpr (sizeof(R) == 8) {
+    for (int e = tid; e < nfk; e += blockDim.x) fkd[e] = ddc_from(sl.fock[e].x, sl.fock[e].y);
+    __syncthreads();
+  }
   for (int z = blockIdx.x; z < nitems; z += gridDim.x) {
     const int item = sl.items[z];
     const int a = item / P, b = item % P;
@@ -650,6 +658,81 @@ __global__ void __launch_bounds__(THETA_WARPS * 32, 2) k_theta(MpoDev st, SlotWS
     C (*As)[TILE + 1] = reinterpret_cast<C (*)[TILE + 1]>(accs);
     C (*Bs)[TILE + 1] = reinterpret_cast<C (*)[TILE + 1]>(accs + TILE * (TILE + 1));
     const int tx = tid & 15, ty = tid >> 4;
+    if constexpr (sizeof(R) == 8) {
+      // the same tiles in double-float: Gamma converted once per staged element, each
+      // k-tile's products summed by four compensated accumulators of at most 16 terms
+      // (Dot2), the weights u(a, b, c, m) and the mixing in double-float
+      ddc (*Ad)[TILE + 1] = reinterpret_cast<ddc (*)[TILE + 1]>(accs);
+      ddc (*Bd)[TILE + 1] = reinterpret_cast<ddc (*)[TILE + 1]>(accs + TILE * (TILE + 1));
+      for (int mc0 = 0; mc0 < nm; mc0 += TMCH) {
+        const int nq = (nm - mc0) < TMCH ? (nm - mc0) : TMCH;
+        for (int i0 = 0; i0 < na; i0 += TILE)
+          for (int j0 = 0; j0 < nb; j0 += TILE) {
+            const int i = i0 + ty, jc = j0 + tx;
+            const bool valid = (i < na) && (jc < nb);
+            ddc acc[TMCH];
+#pragma unroll
+            for (int k = 0; k < TMCH; ++k) acc[k] = ddc_zero();
+            for (int ci = 0; ci < nc; ++ci) {
+              const int cc = ccl[ci], f = cf[ci];
+              const int k0 = segC[cc], k1 = segC[cc + 1];
+              ddc part = ddc_zero();
+              for (int kb = k0; kb < k1; kb += TILE) {
+                const int kn = (k1 - kb) < TILE ? (k1 - kb) : TILE;
+                if (i0 + ty < na && tx < kn) {
+                  const double2 v = G1[(long long)(a0 + i0 + ty) * D + kb + tx];
+                  Ad[ty][tx] = ddc_from(v.x, v.y);
+                } else {
+                  Ad[ty][tx] = ddc_zero();
+                }
+                if (ty < kn && j0 + tx < nb) {
+                  const double2 v = cscale(G2[(long long)(kb + ty) * D + b0 + j0 + tx], lC[kb + ty]);
+                  Bd[ty][tx] = ddc_from(v.x, v.y);
+                } else {
+                  Bd[ty][tx] = ddc_zero();
+                }
+                __syncthreads();
+                if (valid) {
+                  dd_acc rr = dd_acc_zero(), ii = dd_acc_zero(), ri = dd_acc_zero(), ir = dd_acc_zero();
+                  for (int kk = 0; kk < kn; ++kk) {
+                    const ddc x = Ad[ty][kk], y = Bd[kk][tx];
+                    dd_acc_mac(rr, x.re, y.re);
+                    dd_acc_mac(ii, x.im, y.im);
+                    dd_acc_mac(ri, x.re, y.im);
+                    dd_acc_mac(ir, x.im, y.re);
+                  }
+                  part = ddc_add(part, ddc_make(dd_sub(dd_acc_value(rr), dd_acc_value(ii)),
+                                                dd_add(dd_acc_value(ri), dd_acc_value(ir))));
+                }
+                __syncthreads();
+              }
+              if (valid) {
+#pragma unroll
+                for (int k = 0; k < TMCH; ++k) {
+                  if (k < nq) {
+                    const int m = sl.f(BF_M, ml[mc0 + k]);
+                    const ddc w = ddc_mul(fkd[fock_off(dk) + (ca - pair_c(m, ncap)) * (dk + 1) + (f & 0xffff)],
+                                          ddc_conj(fkd[fock_off(db) + (cba - pair_cb(m, ncap)) * (db + 1) + (f >> 16)]));
+                    acc[k] = ddc_add(acc[k], ddc_mul(w, part));
+                  }
+                }
+              }
+            }
+            if (valid) {
+              const double sc = lA[a0 + i] * lB[b0 + jc];
+#pragma unroll
+              for (int k = 0; k < TMCH; ++k) {
+                if (k < nq) {
+                  const int t = ml[mc0 + k];
+                  const double2 v = make_double2(dd_to(acc[k].re), dd_to(acc[k].im));
+                  Th[sl.f(BF_TOFF, t) + (long long)(mr[mc0 + k] + i) * sl.f(BF_C, t) + (mc[mc0 + k] + jc)] =
+                      cvt<C>(cscale(v, sc));
+                }
+              }
+            }
+          }
+      }
+    } else
     for (int mc0 = 0; mc0 < nm; mc0 += TMCH) {
       const int nq = (nm - mc0) < TMCH ? (nm - mc0) : TMCH;
       for (int i0 = 0; i0 < na; i0 += TILE)
