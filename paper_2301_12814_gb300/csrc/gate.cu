@@ -2197,6 +2197,29 @@ __device__ __forceinline__ ddc ddc_dot(const ddc* a, long long sa, const ddc* b,
 }
 
 // Largest column norm^2 of the columns [k0, k1) of W over the cluster (FP64 rounding).
+// One element of a Newton-Schulz step V <- V (3 I - S) / 2 = V - V E / 2 with
+// S = V^dag V (double-float, column-major n x n) and E = S - I: element (i, b) of the
+// new V.  |E| is the non-orthogonality of V (~1e-6 after the FP32 seed, ~1e-11 after
+// one step), so V E is formed in FP32 from the high parts: its rounding is below
+// 1e-7 |E| sqrt(n), which the next step (or, after the second, the double-float
+// precision itself) absorbs, and the correction is added to v_ib by one TwoSum per
+// component.  The product costs n complex FP32 FMAs instead of n complex
+// double-float ones.
+__device__ __forceinline__ ddc ns_update(const ddc* V, const ddc* S, int n, int b, int i) {
+  float cr = 0.f, ci = 0.f;
+  const ddc* sb = S + (long long)b * n;
+  for (int a = 0; a < n; ++a) {
+    const ddc sv = sb[a];
+    const float er = a == b ? (sv.re.hi - 1.f) + sv.re.lo : sv.re.hi;  // hi - 1 is exact near 1
+    const float ei = sv.im.hi;
+    const ddc v = V[(long long)a * n + i];
+    cr = fmaf(v.re.hi, er, fmaf(-v.im.hi, ei, cr));
+    ci = fmaf(v.re.hi, ei, fmaf(v.im.hi, er, ci));
+  }
+  const ddc v = V[(long long)b * n + i];
+  return ddc_make(dd_add_f(v.re, -0.5f * cr), dd_add_f(v.im, -0.5f * ci));
+}
+
 __device__ double cluster_max_norm2_dd(cg::cluster_group& cl, const ddc* W, int h, int k0, int k1, int* hdr,
                                        double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
@@ -2255,28 +2278,9 @@ __device__ int polish_dd(cg::cluster_group& cl, const MpoDev& st, const Slot& sl
       Sd[(long long)a * n + k] = ddc_conj(v);
     }
     cluster_exchange(cl);
-    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {  // T[:, k] = V (3 e_k - S[:, k]) / 2
+    for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
       const int k = k0 + (int)(e / n), i = (int)(e % n);
-      dd tr = dd_zero(), ti = dd_zero();
-      for (int a0 = 0; a0 < n; a0 += 16) {
-        dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
-        const int a1 = min(n, a0 + 16);
-        for (int a = a0; a < a1; ++a) {
-          const ddc sv = Sd[(long long)k * n + a];
-          // w = 1.5 delta_ak - 0.5 S[a, k]  (halving is exact)
-          dd wr = dd_make(-0.5f * sv.re.hi, -0.5f * sv.re.lo);
-          const dd wi = dd_make(-0.5f * sv.im.hi, -0.5f * sv.im.lo);
-          if (a == k) wr = dd_add(wr, dd_make(1.5f, 0.f));
-          const ddc v = Vd[(long long)a * n + i];
-          dd_acc_mac(ar, v.re, wr);
-          dd_acc_mac(ar, dd_neg(v.im), wi);
-          dd_acc_mac(ai, v.re, wi);
-          dd_acc_mac(ai, v.im, wr);
-        }
-        tr = dd_add(tr, dd_acc_value(ar));
-        ti = dd_add(ti, dd_acc_value(ai));
-      }
-      Td[(long long)k * n + i] = ddc_make(tr, ti);
+      Td[(long long)k * n + i] = ns_update(Vd, Sd, n, k, i);
     }
     cluster_exchange(cl);
     for (long long e = tid; e < (long long)(k1 - k0) * n; e += nth) {
@@ -2632,28 +2636,7 @@ __device__ void refine_block_dd(const MpoDev& st, const Slot& sl, const GateDesc
         S[(long long)a * n + b] = ddc_conj(v);
       }
       __syncthreads();
-      for (int e = tid; e < n * n; e += nth) {  // T[:, b] = V (3 e_b - S[:, b]) / 2
-        const int b = e / n, i = e % n;
-        dd tr = dd_zero(), ti = dd_zero();
-        for (int a0 = 0; a0 < n; a0 += 16) {
-          dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
-          const int a1 = min(n, a0 + 16);
-          for (int a = a0; a < a1; ++a) {
-            const ddc sv = S[(long long)b * n + a];
-            dd wr = dd_make(-0.5f * sv.re.hi, -0.5f * sv.re.lo);
-            const dd wi = dd_make(-0.5f * sv.im.hi, -0.5f * sv.im.lo);
-            if (a == b) wr = dd_add(wr, dd_make(1.5f, 0.f));
-            const ddc v = gVc[(long long)a * n + i];
-            dd_acc_mac(ar, v.re, wr);
-            dd_acc_mac(ar, dd_neg(v.im), wi);
-            dd_acc_mac(ai, v.re, wi);
-            dd_acc_mac(ai, v.im, wr);
-          }
-          tr = dd_add(tr, dd_acc_value(ar));
-          ti = dd_add(ti, dd_acc_value(ai));
-        }
-        T[e] = ddc_make(tr, ti);
-      }
+      for (int e = tid; e < n * n; e += nth) T[e] = ns_update(gVc, S, n, e / n, e % n);
       __syncthreads();
       for (int e = tid; e < n * n; e += nth) gVc[e] = T[e];
       __syncthreads();
