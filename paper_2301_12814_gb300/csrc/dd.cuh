@@ -36,12 +36,19 @@
 #define DD_MUL(a, b) __fmul_rn((a), (b))
 #define DD_FMA(a, b, c) __fmaf_rn((a), (b), (c))
 #define DD_RSQRT(a) rsqrtf(a)
+#define DD_F2I(a) __float_as_int(a)
+#define DD_I2F(a) __int_as_float(a)
 #else
 #define DD_ADD(a, b) ((a) + (b))
 #define DD_SUB(a, b) ((a) - (b))
 #define DD_MUL(a, b) ((a) * (b))
 #define DD_FMA(a, b, c) fmaf((a), (b), (c))
 #define DD_RSQRT(a) (1.0f / sqrtf(a))
+#include <string.h>
+static inline int dd_f2i_host(float a) { int i; memcpy(&i, &a, sizeof i); return i; }
+static inline float dd_i2f_host(int i) { float a; memcpy(&a, &i, sizeof a); return a; }
+#define DD_F2I(a) dd_f2i_host(a)
+#define DD_I2F(a) dd_i2f_host(a)
 #endif
 
 struct dd {
@@ -168,3 +175,104 @@ __host__ __device__ __forceinline__ ddc ddc_lin(dd c, ddc x, dd s, ddc y) {
   return ddc_make(dd_dot2(c, x.re, s, y.re), dd_dot2(c, x.im, s, y.im));
 }
 
+// ---- Jacobi rotations of complex double-float column pairs (the FP64 path's one-sided
+// refinement).  A pair (a, b) with squared norms al, be and inner product g = a^dag b
+// is rotated so that a'^dag b' = 0: t = tan(angle) from tau = (be - al) / 2|g|, the
+// cosine c and sine s = t c, and the unit phase e = g / |g|.
+
+// Rotation parameters of a double-float column pair on the FP32 pipe (GB300 runs FP64
+// at 1/61 of the FP32 rate, and the cluster sweeps form them in every lane of the
+// pair's warp).  The decision and angle of the FP64 sweeps: rotate when both columns
+// are above the floor and |g| exceeds tol_abs and os_rel sqrt(al be); tau =
+// (be - al) / 2|g| with be - al in double-float, t = tan(angle) rounded to FP32.  Then
+// c = 1 / sqrt(1 + t^2) and s = t c in double-float (1 + t^2 exact, dd_rsqrt), and the
+// unit phase e = g / |g| in double-float from g scaled by a power of two (exact) so
+// that |g|^2 neither underflows nor overflows.  r2 = |g|^2 / (al be) for the sweep stop.
+__host__ __device__ __forceinline__ float pow2_recip(float m) {  // 2^-E with m in [2^E, 2^(E+1)), m > 0 finite
+  const int ex = (DD_F2I(m) >> 23) & 0xff;
+  return DD_I2F((254 - (ex > 0 ? ex : 1)) << 23);
+}
+__host__ __device__ __forceinline__ bool dd_os_params(dd al, dd be, dd gr, dd gi, bool selfm, float tol_abs,
+                                                      float col_floor, float os_rel, dd& c, dd& s, ddc& e, dd& gabs,
+                                                      float& r2) {
+  if (selfm) gi = dd_zero();
+  const float a = al.hi, b = be.hi;
+  const float gf = selfm ? fabsf(gr.hi) : hypotf(gr.hi, gi.hi);
+  const bool above = a > col_floor && b > col_floor;
+  const float rel = above ? gf * DD_RSQRT(a) * DD_RSQRT(b) : 0.f;
+  r2 = rel * rel;
+  if (!(above && gf > tol_abs && rel > os_rel)) return false;
+  const float tau = 0.5f * dd_sub(be, al).hi / gf;
+  if (!(fabsf(tau) < 1e30f)) return false;  // angle below any representable rotation
+  const float af = fabsf(tau);
+  const float t = (tau >= 0.f ? 1.f : -1.f) * (af > 1e4f ? 0.5f / af : 1.f / (af + sqrtf(1.f + tau * tau)));
+  const float p = DD_MUL(t, t), pe = DD_FMA(t, t, -p);
+  c = dd_rsqrt(dd_add_f(dd_add_f(dd_make(1.f, 0.f), p), pe));
+  s = dd_mul(dd_make(t, 0.f), c);
+  if (selfm) {
+    const bool neg = gr.hi < 0.f;
+    e = ddc_make(dd_make(neg ? -1.f : 1.f, 0.f), dd_zero());
+    gabs = neg ? dd_neg(gr) : gr;
+  } else {
+    const float sc = pow2_recip(fmaxf(fabsf(gr.hi), fabsf(gi.hi))), isc = 1.f / sc;
+    const dd xr = dd_make(gr.hi * sc, gr.lo * sc), xi = dd_make(gi.hi * sc, gi.lo * sc);
+    const dd g2 = dd_add(dd_mul(xr, xr), dd_mul(xi, xi));  // in [1, 8)
+    const dd inv = dd_rsqrt(g2);
+    e = ddc_make(dd_mul(xr, inv), dd_mul(xi, inv));
+    const dd gs = dd_mul(g2, inv);
+    gabs = dd_make(gs.hi * isc, gs.lo * isc);
+  }
+  return true;
+}
+// Squared column norms after the rotation (c, s, e) of a pair with norms al, be and
+// inner product g: with b~ = conj(e) b, a^dag b~ = |g|, so
+//   |a'|^2 = c^2 al + s^2 be - 2 c s |g|,  |b'|^2 = s^2 al + c^2 be + 2 c s |g|
+// (both rotation forms of ddc_rotate_dd give these).  The double-float sweeps carry the
+// norms this way from pair to pair and recompute them at the start of every sweep,
+// so a sweep forms one inner product per pair instead of three.
+__host__ __device__ __forceinline__ void rotated_norms_dd(dd& al, dd& be, dd gabs, dd c, dd s) {
+  const dd cc = dd_mul(c, c), ss = dd_mul(s, s);
+  dd x = dd_mul(dd_mul(c, s), gabs);
+  x = dd_add(x, x);
+  const dd a2 = dd_sub(dd_add(dd_mul(cc, al), dd_mul(ss, be)), x);
+  const dd b2 = dd_add(dd_add(dd_mul(ss, al), dd_mul(cc, be)), x);
+  al = a2;
+  be = b2;
+}
+
+// Rotation angles below this apply through FP32 corrections (ddc_rotate_dd).
+constexpr double DD_SMALL_ROT = 1e-7;
+
+// Apply the rotation (c, s, e) to the column pair (x, y) in double-float, elements
+// lane, lane + 32, ... < len.  Large angles: x' = c x - s conj(e) y, y' = s x + c conj(e) y
+// (the column-q phase form of the FP64 path).  Angles |s| < DD_SMALL_ROT: the
+// phase-free rotation x' = c x - s conj(e) y, y' = c y + s e x -- the same unitary up
+// to the phase conj(e) on column q, a gauge that W and V share (the product W V^dag,
+// and with it X and Y of the re-split, is unchanged) -- written as x + dx, y + dy with
+// dx = (c - 1) x - s conj(e) y and dy = (c - 1) y + s e x formed in FP32 from the high
+// parts: |dx|, |dy| <= ~1e-7 |x, y|, so the FP32 rounding and the neglected low parts
+// stay near 1e-14 relative, and an element costs a TwoSum per component instead of two
+// double-float products.
+__host__ __device__ __forceinline__ void ddc_rotate_dd(ddc* x, ddc* y, int len, int lane, dd c, dd s, ddc e) {
+  if (fabsf(s.hi) < (float)DD_SMALL_ROT) {
+    const float cm1 = (c.hi - 1.f) + c.lo, sf = s.hi;  // c.hi - 1 is exact (Sterbenz)
+    const float er = e.re.hi, ei = e.im.hi;
+    for (int k = lane; k < len; k += 32) {
+      const ddc a = x[k], b = y[k];
+      const float ceb_r = er * b.re.hi + ei * b.im.hi, ceb_i = er * b.im.hi - ei * b.re.hi;  // conj(e) b
+      const float ea_r = er * a.re.hi - ei * a.im.hi, ea_i = er * a.im.hi + ei * a.re.hi;    // e a
+      const float dxr = cm1 * a.re.hi - sf * ceb_r, dxi = cm1 * a.im.hi - sf * ceb_i;
+      const float dyr = cm1 * b.re.hi + sf * ea_r, dyi = cm1 * b.im.hi + sf * ea_i;
+      x[k] = ddc_make(dd_add_f(a.re, dxr), dd_add_f(a.im, dxi));
+      y[k] = ddc_make(dd_add_f(b.re, dyr), dd_add_f(b.im, dyi));
+    }
+    return;
+  }
+  const dd msd = dd_neg(s);
+  const ddc ec = ddc_conj(e);
+  for (int k = lane; k < len; k += 32) {
+    const ddc a = x[k], bs = ddc_mul(y[k], ec);
+    x[k] = ddc_lin(c, a, msd, bs);
+    y[k] = ddc_lin(s, a, c, bs);
+  }
+}
