@@ -57,15 +57,20 @@ typedef enum {
 } mpo_status;
 
 typedef enum {
-  MPO_FP64 = 0,        /* Theta, Jacobi refinement, re-split in float64 / complex128;
-                          the Gram matrix and the Jacobi seed that only starts the
-                          refinement are FP32                                             */
-  MPO_MIXED_TF32 = 1,  /* mixed: Theta contraction, Gram, Jacobi seed and one-sided
-                          refinement in FP32 (SIMT FMA, FP32 accumulation); keep-chi
-                          selection, discarded weight, lambda, entropy, observables and
-                          the stored Gamma in FP64                                        */
-  MPO_MIXED_BF16 = 2   /* accepted as a name for the BF16 form; computes exactly as
-                          MPO_MIXED_TF32 (no BF16 operand path is built)                 */
+  MPO_FP64 = 0,        /* FP64-accurate: Theta contraction in FP64 (its large items in
+                          double-float arithmetic on the FP32 pipe), the Jacobi
+                          refinement (Newton-Schulz, W = Theta V, one-sided sweeps) in
+                          double-float (about 48 significand bits), re-split, lambda and
+                          observables in float64 / complex128; the Gram matrix (3xTF32
+                          tensor cores from a Gram side of 48, FP32 below) and the Jacobi
+                          seed that only starts the refinement are FP32                   */
+  MPO_MIXED_TF32 = 1,  /* mixed: Theta contraction (FP32 SIMT two-stage; 3xTF32 tensor
+                          cores by launch choice), Gram, Jacobi seed and one-sided
+                          refinement in FP32 (FP32 accumulation); keep-chi selection,
+                          discarded weight, lambda, entropy, observables and the stored
+                          Gamma in FP64                                                   */
+  MPO_MIXED_BF16 = 2   /* as MPO_MIXED_TF32, with the Theta contraction on the tensor
+                          cores in BF16 (one BF16 pass per operand, FP32 accumulation)   */
 } mpo_precision;
 
 typedef struct {
