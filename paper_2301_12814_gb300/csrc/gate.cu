@@ -2083,51 +2083,8 @@ __device__ void cluster_rank(cg::cluster_group& cl, const MpoDev& st, const Slot
 // products are summed in chunks of 16 by compensated accumulation and the chunks
 // combined by dd_add, which bounds their error by ~20 u^2 times the magnitude sum.
 
-// sum_{i < len} conj(a[i sa]) b[i sb] (conj_a) or a[i sa] b[i sb], in double-float
-__device__ __forceinline__ ddc ddc_dot(const ddc* a, long long sa, const ddc* b, long long sb, int len,
-                                       bool conj_a) {
-  dd tr = dd_zero(), ti = dd_zero();
-  for (int i0 = 0; i0 < len; i0 += 16) {
-    dd_acc ar = dd_acc_zero(), ai = dd_acc_zero();
-    const int i1 = min(len, i0 + 16);
-    for (int i = i0; i < i1; ++i) {
-      const ddc x = a[(long long)i * sa], y = b[(long long)i * sb];
-      const dd xi = conj_a ? dd_neg(x.im) : x.im;
-      dd_acc_mac(ar, x.re, y.re);
-      dd_acc_mac(ar, dd_neg(xi), y.im);
-      dd_acc_mac(ai, x.re, y.im);
-      dd_acc_mac(ai, xi, y.re);
-    }
-    tr = dd_add(tr, dd_acc_value(ar));
-    ti = dd_add(ti, dd_acc_value(ai));
-  }
-  return ddc_make(tr, ti);
-}
 
 // Largest column norm^2 of the columns [k0, k1) of W over the cluster (FP64 rounding).
-// One element of a Newton-Schulz step V <- V (3 I - S) / 2 = V - V E / 2 with
-// S = V^dag V (double-float, column-major n x n) and E = S - I: element (i, b) of the
-// new V.  |E| is the non-orthogonality of V (~1e-6 after the FP32 seed, ~1e-11 after
-// one step), so V E is formed in FP32 from the high parts: its rounding is below
-// 1e-7 |E| sqrt(n), which the next step (or, after the second, the double-float
-// precision itself) absorbs, and the correction is added to v_ib by one TwoSum per
-// component.  The product costs n complex FP32 FMAs instead of n complex
-// double-float ones.
-__device__ __forceinline__ ddc ns_update(const ddc* V, const ddc* S, int n, int b, int i) {
-  float cr = 0.f, ci = 0.f;
-  const ddc* sb = S + (long long)b * n;
-  for (int a = 0; a < n; ++a) {
-    const ddc sv = sb[a];
-    const float er = a == b ? (sv.re.hi - 1.f) + sv.re.lo : sv.re.hi;  // hi - 1 is exact near 1
-    const float ei = sv.im.hi;
-    const ddc v = V[(long long)a * n + i];
-    cr = fmaf(v.re.hi, er, fmaf(-v.im.hi, ei, cr));
-    ci = fmaf(v.re.hi, ei, fmaf(v.im.hi, er, ci));
-  }
-  const ddc v = V[(long long)b * n + i];
-  return ddc_make(dd_add_f(v.re, -0.5f * cr), dd_add_f(v.im, -0.5f * ci));
-}
-
 __device__ double cluster_max_norm2_dd(cg::cluster_group& cl, const ddc* W, int h, int k0, int k1, int* hdr,
                                        double* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;

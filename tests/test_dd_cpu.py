@@ -5,8 +5,9 @@ combined pairwise) with long double on random inputs, some near cancellation, an
 fails if an error exceeds a small multiple of u^2 = 2^-48 (relative to the operands'
 magnitudes); tests/c_abi/dd_rot_check.cpp does the same for the one-sided Jacobi
 rotation of a complex double-float column pair (parameters on the FP32 pipe, both
-rotation forms, carried norms).  Built here with the host compiler, FMA contraction
-off."""
+rotation forms, carried norms), and tests/c_abi/dd_ns_check.cpp for the two
+Newton-Schulz steps that orthonormalise the FP32 seed.  Built here with the host
+compiler, FMA contraction off."""
 import os
 import shutil
 import subprocess
@@ -45,5 +46,13 @@ def test_double_float_jacobi_rotation(tmp_path):
     to the FP32-rounded angle (1e-6 relative), the pair's total norm kept, and the
     carried norms equal to the rotated columns' norms, for large and small angles."""
     out = _build_and_run(tmp_path, "dd_rot_check")
+    assert out.returncode == 0, out.stdout
+
+
+def test_double_float_newton_schulz(tmp_path):
+    """Two Newton-Schulz steps (S in double-float, the correction product in FP32) take
+    an FP32 seed with 1e-6 non-orthogonality to |V^dag V - I| <= 5e-14, within 1e-11 of
+    the same steps in long double."""
+    out = _build_and_run(tmp_path, "dd_ns_check")
     assert out.returncode == 0, out.stdout
 
